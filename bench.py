@@ -1,0 +1,340 @@
+#!/usr/bin/env python
+"""Benchmark of the VG-rtTDDFTB propagation step on GB300.
+
+Workload: 512-atom silicon-like supercell (4x4x4 diamond cells, Gaussian
+displacements sigma = 0.3 bohr, sp3 basis, N = 2048 orbitals), Gamma point,
+delta kick A_x = 0.001 a.u., dt = 0.2 a.u., SCC on (synthetic inputs from
+paper_2308_09782_gb300.inputs, config "si512_kick").  One step = one leapfrog
+step of the whole hot path: Mulliken/current/energy reductions, SCC shift,
+Bloch-sum phase build, both commutator products, leapfrog update.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+Prints one JSON line (rank 0).  value = steps/s of the split-precision
+(tcgen05 BF16x3, delta form) path summed over ranks (independent replicas);
+the plain FP64 path and the J(t) error of the split path against it are
+reported beside it.  --impl reference times the CPU oracle on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "steps/s at 512-atom Si: FP64 vs split-precision @ J err≤1e-4; % of peak"
+CONFIG = "si512_kick"
+WORKLOAD = ("512-atom Si supercell (diamond 4x4x4, sigma=0.3 bohr), sp3, N=2048 orbitals, Gamma, "
+            "kick A_x=0.001 au, dt=0.2 au, SCC on")
+AU_FS = 0.0241888432658
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=300)
+    p.add_argument("--warmup", type=int, default=10)
+    p.add_argument("--impl", choices=["native", "reference"], default="native")
+    p.add_argument("--fp64-steps", type=int, default=20)
+    p.add_argument("--cpu-steps", type=int, default=6)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (one process per GPU; independent replicas)
+# ---------------------------------------------------------------------------
+def dist_setup(use_cuda: bool):
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if use_cuda:
+        torch.cuda.set_device(local)
+    if world > 1 and not dist.is_initialized():
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl" if use_cuda else "gloo")
+    return rank, world, local
+
+
+def barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+def max_over_ranks(x: float) -> float:
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return x
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# roofline helpers
+# ---------------------------------------------------------------------------
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        return {}
+
+
+def kernel_traffic(kernel: str, per_launch_units: float):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel source
+    is unchanged since the capture; None otherwise."""
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[kernel]
+    except (OSError, KeyError, ValueError):
+        return None
+    src = os.path.join(ROOT, rec["source"])
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    if h != rec["sha256"]:
+        return None
+    return rec["bytes_per_unit"] * per_launch_units
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle baseline (bounded sample)
+# ---------------------------------------------------------------------------
+def cpu_baseline(nsteps: int, sysd=None, A=None):
+    import oracle as O
+    from paper_2308_09782_gb300 import inputs
+    if sysd is None:
+        sysd, A, _ = inputs.config(CONFIG)
+    t0 = time.perf_counter()
+    ctx = O.setup(sysd)
+    nocc = int(round(sysd["n_electrons"] / 2))
+    eps0 = np.zeros(int(sysd["orb_offset"][-1]))
+    D0 = [O.density_from_hamiltonian(O.hamiltonian(H0, S, P, np.zeros(3), eps0), S, nocc)[0]
+          for S, H0, P in zip(ctx["S"], ctx["H0"], ctx["P"])]
+    t_setup = time.perf_counter() - t0
+    O.propagate(sysd, A, 1, D0, ctx=ctx)            # warm-up (one step)
+    t1 = time.perf_counter()
+    O.propagate(sysd, A, nsteps, D0, ctx=ctx)
+    dt = time.perf_counter() - t1
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {"value": nsteps / dt, "unit": "steps/s", "cores": cores, "kind": "oracle",
+            "sample": f"{nsteps} oracle steps (plus 1 warm-up) of {CONFIG} (N=2048, Gamma) from a non-SCC "
+                      f"start density; numpy complex128, OpenBLAS threads = {cores} cores; "
+                      f"setup {t_setup:.1f} s not timed"}
+
+
+# ---------------------------------------------------------------------------
+# native (GPU) arm
+# ---------------------------------------------------------------------------
+def native(args):
+    import torch
+    from paper_2308_09782_gb300 import inputs, vgtb
+    rank, world, local = dist_setup(True)
+    vgtb.load()
+    sysd, A, _ = inputs.config(CONFIG)
+    K, W = args.steps, max(args.warmup, 3)
+    n_need = W + K + 1
+    if A.shape[0] < n_need:                      # the kick is constant after t = 0
+        A = np.tile(A[:1], (n_need, 1))
+    stream = torch.cuda.current_stream()
+    ctx = vgtb.Context(sysd, precision=vgtb.SPLIT_BF16X3, init=vgtb.INIT_GROUND,
+                       cuda_stream=stream.cuda_stream, graph_steps=50)
+    ctx.set_field(0, A[:n_need])
+    ctx.profile(True)
+    ctx.propagate(W)
+    ctx.profile(True)                            # reset the per-kernel counters
+    clk = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    clk.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ctx.propagate(K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = clk.stop()
+    ms = max_over_ranks(e0.elapsed_time(e1))
+    stats = ctx.kernel_stats()
+    J_split, _, _ = ctx.observables(0, charges=False)
+    D0 = ctx.get_initial_density(0, 0)
+
+    # plain FP64 path on the same ground state
+    Kf = args.fp64_steps
+    cf = vgtb.Context(sysd, precision=vgtb.FP64, init=vgtb.INIT_USER, cuda_stream=stream.cuda_stream,
+                      graph_steps=1)
+    cf.set_density(0, 0, D0)
+    cf.set_field(0, A[:Kf + 3])
+    cf.propagate(2)
+    torch.cuda.synchronize()
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    cf.propagate(Kf)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    ms_f = max_over_ranks(f0.elapsed_time(f1))
+    J_f, _, _ = cf.observables(0, charges=False)
+    cf.close()
+    nj = min(len(J_f), len(J_split))
+    j_err = float(np.linalg.norm(J_split[:nj] - J_f[:nj]) / np.linalg.norm(J_f[:nj]))
+
+    # end to end through the C-ABI: pinned host A table in, J/E/q series out
+    e2e = None
+    if not args.no_e2e:
+        Ah = torch.from_numpy(np.ascontiguousarray(A[:K + 1])).pin_memory().numpy()
+        nat = len(sysd["z_ref"])
+        outJ = torch.empty((K + 1, 3), dtype=torch.float64).pin_memory().numpy()
+        outE = torch.empty((K + 1,), dtype=torch.float64).pin_memory().numpy()
+        outQ = torch.empty((K + 1, nat), dtype=torch.float64).pin_memory().numpy()
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.set_field(0, Ah)
+        ctx.propagate(K)
+        ctx.observables_into(0, outJ, outE, outQ)
+        t_e2e = max_over_ranks(time.perf_counter() - t0)
+        e2e = {"value": world * K / t_e2e, "unit": "steps/s",
+               "h2d_bytes_per_step": int(Ah.nbytes / K),
+               "d2h_bytes_per_step": int((outJ.nbytes + outE.nbytes + outQ.nbytes) / K)}
+    ctx.close()
+
+    N = int(sysd["orb_offset"][-1])
+    Np = (N + 127) // 128 * 128
+    flops1 = 3 * 2 * Np * (2 * Np) * (4 * Np)      # executed BF16 flops, product 1 (K' = 2 x 2Np)
+    flops2 = 3 * 2 * Np * (2 * Np) * (2 * Np)      # product 2
+    g1_n, g1_ms = stats["gemm1"]
+    g2_n, g2_ms = stats["gemm2"]
+    peaks = measured_peaks()
+    peak = peaks.get("bf16_tflops_sustained")
+    peak_kind = "measured sustained bf16 (MEASURED_PEAKS.json)"
+    if peak is None:
+        peak, peak_kind = 1700.0, "fallback sustained bf16"
+    avg1 = g1_ms / max(g1_n, 1)
+    ach1 = flops1 / (avg1 * 1e-3) / 1e12
+    ach2 = flops2 / (g2_ms / max(g2_n, 1) * 1e-3) / 1e12
+    step_ms = ms / K
+    value = world * K / (ms / 1e3)
+    kern_ms = {k: (v[1] / max(v[0], 1)) for k, v in stats.items()}
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.cpu_steps)
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": "steps/s", "n_gpus": world, "steps": K,
+        "warmup": W, "ms_per_step": round(step_ms, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16x3 (f32 accumulate) + f64 master", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "name": CONFIG, "precision": "split_bf16x3 delta form",
+                   "parallelism": f"{world} independent replica(s)",
+                   "l2": "working set ~0.6 GB per step, larger than the 129 MB L2 (no flush)",
+                   "fs_per_hour": round(value / world * 0.2 * AU_FS * 3600, 2)},
+        "fp64": {"value": round(world * Kf / (ms_f / 1e3), 3), "unit": "steps/s", "steps": Kf,
+                 "ms_per_step": round(ms_f / Kf, 3),
+                 "fs_per_hour": round(Kf / (ms_f / 1e3) * 0.2 * AU_FS * 3600, 3)},
+        "j_rel_err_split_vs_fp64": j_err, "j_err_steps": nj - 1,
+        "roofline": {"bound": "tensor", "kernel": "k_tc_gemm (product 1: W = [dD|D0][H|dH]^dagger)",
+                     "achieved": round(ach1, 1), "peak": peak, "unit": "TFLOP/s",
+                     "frac": round(ach1 / peak, 4), "peak_kind": peak_kind,
+                     "traffic": kernel_traffic("tc_gemm1", 1.0),
+                     "flops_per_launch": flops1, "avg_launch_ms": round(avg1, 4),
+                     "product2_achieved": round(ach2, 1), "product2_frac": round(ach2 / peak, 4)},
+        "kernel_ms_per_step": {k: round(v, 4) for k, v in kern_ms.items()},
+        "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": 6 * K + 2,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the CPU oracle on the host cores
+# ---------------------------------------------------------------------------
+def reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    steps = max(1, min(args.steps, 40))
+    cpu = cpu_baseline(steps)
+    v = cpu["value"]
+    line = {"metric": METRIC, "value": round(v, 5), "unit": "steps/s", "n_gpus": 0, "steps": steps,
+            "warmup": 1, "ms_per_step": round(1e3 / v, 2), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "name": CONFIG},
+            "cpu_baseline": cpu,
+            "e2e": {"value": round(v, 5), "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        reference(a)
+    else:
+        native(a)

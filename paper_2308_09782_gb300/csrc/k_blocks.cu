@@ -1,0 +1,393 @@
+// Block-sparse kernels of one propagation step:
+//   k_obs   - Mulliken, current and energy partial sums from D_k(t_n) (Eqs. 10, 14)
+//   k_scc   - per-trajectory reduction: dq, eps = gamma dq, J, E (Eq. 10, Eq. 14)
+//   k_phase - Bloch sum of H_k(t_n) with the vector potential (Eqs. 7-12)
+// One warp handles one target (I, J) of one trajectory: it walks the target's
+// real-space images (blocks with different L), lanes over the n_I x n_J
+// elements, so the block values are read once, coalesced, per step.
+// All reductions use fixed orders (lane butterflies, strided loops, fixed
+// trees), so reruns are bitwise identical.
+#include "vgtb_internal.h"
+
+namespace vgtb {
+
+__device__ __forceinline__ int find_traj(const int* pre, int n, int w) {
+  int lo = 0, hi = n;  // pre[lo] <= w < pre[hi]
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (pre[mid] <= w) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// Partial sums per target, summed over k with weights w_k:
+//   q   : sum Re(D_{mu nu} conj(S_k,mu nu))                 (Eq. 10: [D S]_{mu mu})
+//   T_a : sum Re(D_{mu nu} conj(Pi^a_k,mu nu))              (Eq. 14: Tr[D Pi^a])
+//   E   : sum Re(D_{mu nu} conj((H0 + (A/c).P + |A|^2/2c^2 S)_{mu nu}))
+// With u = D e^{+i k.L} (conjugated phase) an image contributes
+//   q += s Re u,  T_a += ds_a Im u + (A_a/c) s Re u,
+//   E += (h0 + alpha s) Re u + ((A/c).ds) Im u,   because P = i dS/dR_J.
+// ---------------------------------------------------------------------------
+__global__ void k_obs(const DevSys* __restrict__ sysv, const DevTraj* __restrict__ trj,
+                      const DevItem* __restrict__ items, const int* __restrict__ wpre, int n_traj,
+                      int total, const int* __restrict__ step, int delta, int fixed_step) {
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= total) return;
+  const int t = find_traj(wpre, n_traj, w);
+  const int tg = w - wpre[t];
+  const DevTraj& T = trj[t];
+  const DevSys& S = sysv[T.sys];
+  const int n = fixed_step >= 0 ? fixed_step : *step;
+  const int par = n & 1;
+  double A0 = 0.0, A1 = 0.0, A2 = 0.0;
+  if (T.A) {
+    A0 = T.A[3 * n];
+    A1 = T.A[3 * n + 1];
+    A2 = T.A[3 * n + 2];
+  }
+  const double ic = 1.0 / kLight;
+  const double alpha = (A0 * A0 + A1 * A1 + A2 * A2) * 0.5 * ic * ic;
+  const int I = S.tgt_I[tg], J = S.tgt_J[tg];
+  const int oi = S.orb_off[I], ni = S.orb_off[I + 1] - oi;
+  const int oj = S.orb_off[J], nj = S.orb_off[J + 1] - oj;
+  const int nel = ni * nj;
+  const int g0 = S.tgt_img0[tg], g1 = S.tgt_img0[tg + 1];
+  const long long NN = (long long)S.Np * S.Np;
+  double aq = 0.0, ax = 0.0, ay = 0.0, az = 0.0, ae = 0.0;
+  for (int e = lane; e < nel; e += 32) {
+    const int a = e / nj, b = e - a * nj;
+    const long long idx = (long long)(oi + a) * S.Np + (oj + b);
+    for (int k = 0; k < S.nk; ++k) {
+      const DevItem& it = items[T.item0 + k];
+      double2 d = it.D[par][idx];
+      if (delta) {
+        const double2 d0 = S.D0[k * NN + idx];
+        d.x += d0.x;
+        d.y += d0.y;
+      }
+      const double wk = S.wk[k];
+      double lq = 0.0, lx = 0.0, ly = 0.0, lz = 0.0, le = 0.0;
+      for (int g = g0; g < g1; ++g) {
+        const int blk = S.img_blk[g];
+        const long long off = S.blk_off[blk] + e;
+        const double sv = S.s[off], hv = S.h0[off];
+        const double dx = S.ds[off], dy = S.ds[S.ds_stride + off], dz = S.ds[2 * S.ds_stride + off];
+        const double2 ph = S.phase[(long long)k * S.n_blk + blk];
+        const double ur = d.x * ph.x + d.y * ph.y;
+        const double ui = d.y * ph.x - d.x * ph.y;
+        lq += sv * ur;
+        lx += dx * ui + A0 * ic * sv * ur;
+        ly += dy * ui + A1 * ic * sv * ur;
+        lz += dz * ui + A2 * ic * sv * ur;
+        le += (hv + alpha * sv) * ur + (A0 * dx + A1 * dy + A2 * dz) * ic * ui;
+      }
+      aq += wk * lq;
+      ax += wk * lx;
+      ay += wk * ly;
+      az += wk * lz;
+      ae += wk * le;
+    }
+  }
+  aq = warp_sum(aq);
+  ax = warp_sum(ax);
+  ay = warp_sum(ay);
+  az = warp_sum(az);
+  ae = warp_sum(ae);
+  if (lane == 0) {
+    double* p = T.part + 5LL * tg;
+    p[0] = aq;
+    p[1] = ax;
+    p[2] = ay;
+    p[3] = az;
+    p[4] = ae;
+  }
+}
+
+void launch_obs(const DevSys* sys, const DevTraj* trj, const DevItem* items, const int* warp_prefix,
+                int n_traj, int total_warps, const int* step, int delta, int fixed_step, cudaStream_t st) {
+  const int threads = 256;
+  const int blocks = (total_warps * 32 + threads - 1) / threads;
+  k_obs<<<blocks, threads, 0, st>>>(sys, trj, items, warp_prefix, n_traj, total_warps, step, delta,
+                                    fixed_step);
+}
+
+// ---------------------------------------------------------------------------
+// One CTA per trajectory: q_I = sum of its targets' partials, dq = q - Z,
+// eps = gamma dq (Eq. 10), J_a = -T_a / Omega (Eq. 14), E = E_band + dq.eps/2.
+// ---------------------------------------------------------------------------
+template <int NT>
+__device__ void block_sum5(double (&v)[5], double* sh) {
+  // sh: NT*5 doubles; fixed-tree reduction (deterministic)
+  const int tid = threadIdx.x;
+#pragma unroll
+  for (int i = 0; i < 5; ++i) sh[i * NT + tid] = v[i];
+  __syncthreads();
+  for (int s = NT / 2; s > 0; s >>= 1) {
+    if (tid < s) {
+#pragma unroll
+      for (int i = 0; i < 5; ++i) sh[i * NT + tid] += sh[i * NT + tid + s];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 5; ++i) v[i] = sh[i * NT];
+  __syncthreads();
+}
+
+constexpr int kSccThreads = 256;
+
+__global__ void __launch_bounds__(kSccThreads) k_scc(const DevSys* __restrict__ sysv, DevTraj* trj,
+                                                    int n_traj, const int* __restrict__ step, int stride,
+                                                    int fixed_step, int record) {
+  extern __shared__ double sm[];  // [kSccThreads*5] reduction + [nat] dq
+  const int t = blockIdx.x;
+  if (t >= n_traj) return;
+  DevTraj& T = trj[t];
+  const DevSys& S = sysv[T.sys];
+  const int n = fixed_step >= 0 ? fixed_step : *step;
+  double* red = sm;
+  double* dq = sm + 5 * kSccThreads;
+  const int tid = threadIdx.x;
+  const bool rec_q = record && T.q && (n % stride == 0);
+  double acc[5] = {0, 0, 0, 0, 0};  // sum q, Tx, Ty, Tz, Eband
+  for (int I = tid; I < S.nat; I += kSccThreads) {
+    double q = 0.0;
+    for (int tg = S.atom_tgt0[I]; tg < S.atom_tgt0[I + 1]; ++tg) q += T.part[5LL * tg];
+    dq[I] = q - S.z[I];
+    T.dq[I] = dq[I];
+    acc[0] += q;
+    if (rec_q) T.q[(long long)(n / stride) * S.nat + I] = q;
+  }
+  for (int tg = tid; tg < S.n_tgt; tg += kSccThreads) {
+    acc[1] += T.part[5LL * tg + 1];
+    acc[2] += T.part[5LL * tg + 2];
+    acc[3] += T.part[5LL * tg + 3];
+    acc[4] += T.part[5LL * tg + 4];
+  }
+  __syncthreads();
+  block_sum5<kSccThreads>(acc, red);
+  // eps = gamma dq : one warp per row, fixed lane order
+  const int warp = tid >> 5, lane = tid & 31;
+  double escc = 0.0;
+  for (int I = warp; I < S.nat; I += kSccThreads / 32) {
+    double e = 0.0;
+    const double* g = S.gamma + (long long)I * S.nat;
+    for (int K = lane; K < S.nat; K += 32) e += g[K] * dq[K];
+    e = warp_sum(e);
+    if (lane == 0) T.eps[I] = e;
+    escc += (lane == 0) ? dq[I] * e : 0.0;
+  }
+  double v5[5] = {escc, 0, 0, 0, 0};
+  block_sum5<kSccThreads>(v5, red);
+  if (tid == 0) {
+    const double J0 = -acc[1] / S.omega, J1 = -acc[2] / S.omega, J2 = -acc[3] / S.omega;
+    const double E = acc[4] + 0.5 * v5[0];
+    if (record) {
+      T.J[3LL * n] = J0;
+      T.J[3LL * n + 1] = J1;
+      T.J[3LL * n + 2] = J2;
+      T.E[n] = E;
+    }
+    int st = 0;
+    if (!isfinite(J0) || !isfinite(J1) || !isfinite(J2) || !isfinite(E) || !isfinite(acc[0])) st |= ST_NONFINITE;
+    if (fabs(acc[0] - S.nel) > 1e-6 * fmax(1.0, S.nel)) st |= ST_DRIFT;
+    if (st) atomicOr(T.status, st);
+  }
+}
+
+int scc_configure(int max_nat) {
+  const size_t sm = sizeof(double) * (5 * kSccThreads + (size_t)max_nat);
+  if (sm > 48 * 1024) {
+    if (cudaFuncSetAttribute(k_scc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) return -1;
+  }
+  return 0;
+}
+
+void launch_scc(const DevSys* sys, DevTraj* trj, int n_traj, const int* step, int stride, int fixed_step,
+                int record, int max_nat, cudaStream_t st) {
+  const size_t sm = sizeof(double) * (5 * kSccThreads + (size_t)max_nat);
+  k_scc<<<n_traj, kSccThreads, sm, st>>>(sys, trj, n_traj, step, stride, fixed_step, record);
+}
+
+// ---------------------------------------------------------------------------
+// Phase build: H_k(t)_{mu nu} = sum_images e^{-ik.L} v_{mu nu}(L) with
+//   plain: v = H0 + (alpha + (eps_I + eps_J)/2) S + (i/c) A.dS        (Eqs. 9-12)
+//   delta: H without alpha (its commutator vanishes, Eq. 3 remark) and
+//          dH = ((eps_I-eps0_I) + (eps_J-eps0_J))/2 S + (i/c) A.dS.
+// The split form stores the embedded real matrix [[Re, Im], [-Im, Re]] of H
+// and dH as BF16 hi/lo pieces, the B operand of the first product.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void split_bf16(double x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+  hi = __double2bfloat16(x);
+  lo = __double2bfloat16(x - (double)__bfloat162float(hi));
+}
+
+__device__ __forceinline__ void store_emb(__nv_bfloat16* base, int Np, int r, int c, double re, double im) {
+  // base -> piece 0; piece 1 at + 4 Np^2
+  const long long P = 4LL * Np * Np;
+  const long long ld = 2LL * Np;
+  __nv_bfloat16 rh, rl, ih, il;
+  split_bf16(re, rh, rl);
+  split_bf16(im, ih, il);
+  const long long i00 = (long long)r * ld + c;
+  const long long i01 = (long long)r * ld + Np + c;
+  const long long i10 = (long long)(Np + r) * ld + c;
+  const long long i11 = (long long)(Np + r) * ld + Np + c;
+  base[i00] = rh;
+  base[P + i00] = rl;
+  base[i01] = ih;
+  base[P + i01] = il;
+  base[i10] = __hneg(ih);
+  base[P + i10] = __hneg(il);
+  base[i11] = rh;
+  base[P + i11] = rl;
+}
+
+__global__ void k_phase(const DevSys* __restrict__ sysv, const DevTraj* __restrict__ trj,
+                        const DevItem* __restrict__ items, const int* __restrict__ wpre, int n_traj,
+                        int total, const int* __restrict__ step, int mode, int fixed_step) {
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= total) return;
+  const int t = find_traj(wpre, n_traj, w);
+  const int tg = w - wpre[t];
+  const DevTraj& T = trj[t];
+  const DevSys& S = sysv[T.sys];
+  const int n = fixed_step >= 0 ? fixed_step : *step;
+  double A0 = 0.0, A1 = 0.0, A2 = 0.0;
+  if (T.A) {
+    A0 = T.A[3 * n];
+    A1 = T.A[3 * n + 1];
+    A2 = T.A[3 * n + 2];
+  }
+  const double ic = 1.0 / kLight;
+  const double alpha = (A0 * A0 + A1 * A1 + A2 * A2) * 0.5 * ic * ic;
+  const int I = S.tgt_I[tg], J = S.tgt_J[tg];
+  const int oi = S.orb_off[I], ni = S.orb_off[I + 1] - oi;
+  const int oj = S.orb_off[J], nj = S.orb_off[J + 1] - oj;
+  const int nel = ni * nj;
+  const int g0 = S.tgt_img0[tg], g1 = S.tgt_img0[tg + 1];
+  const double ebar = 0.5 * (T.eps[I] + T.eps[J]);
+  const double beta = (mode == PH_FP64_PLAIN) ? alpha + ebar : ebar;
+  const double dbeta = (mode == PH_FP64_PLAIN) ? 0.0 : 0.5 * ((T.eps[I] - S.eps0[I]) + (T.eps[J] - S.eps0[J]));
+  for (int e = lane; e < nel; e += 32) {
+    const int a = e / nj, b = e - a * nj;
+    const long long idx = (long long)(oi + a) * S.Np + (oj + b);
+    for (int k = 0; k < S.nk; ++k) {
+      double hr = 0.0, hi = 0.0, dr = 0.0, di = 0.0;
+      for (int g = g0; g < g1; ++g) {
+        const int blk = S.img_blk[g];
+        const long long off = S.blk_off[blk] + e;
+        const double sv = S.s[off], hv = S.h0[off];
+        const double adS = (A0 * S.ds[off] + A1 * S.ds[S.ds_stride + off] + A2 * S.ds[2 * S.ds_stride + off]) * ic;
+        const double2 ph = S.phase[(long long)k * S.n_blk + blk];
+        const double vr = hv + beta * sv;  // v = vr + i adS
+        hr += ph.x * vr - ph.y * adS;
+        hi += ph.x * adS + ph.y * vr;
+        const double wr = dbeta * sv;       // dv = wr + i adS
+        dr += ph.x * wr - ph.y * adS;
+        di += ph.x * adS + ph.y * wr;
+      }
+      const DevItem& it = items[T.item0 + k];
+      if (mode == PH_SPLIT) {
+        store_emb(it.Hemb_p, S.Np, oi + a, oj + b, hr, hi);
+        store_emb(it.dHemb_p, S.Np, oi + a, oj + b, dr, di);
+      } else {
+        it.H[idx] = make_double2(hr, hi);
+        if (mode == PH_FP64_DELTA) it.dH[idx] = make_double2(dr, di);
+      }
+    }
+  }
+}
+
+void launch_phase(const DevSys* sys, const DevTraj* trj, const DevItem* items, const int* warp_prefix,
+                  int n_traj, int total_warps, const int* step, int mode, int fixed_step, cudaStream_t st) {
+  const int threads = 256;
+  const int blocks = (total_warps * 32 + threads - 1) / threads;
+  k_phase<<<blocks, threads, 0, st>>>(sys, trj, items, warp_prefix, n_traj, total_warps, step, mode,
+                                      fixed_step);
+}
+
+// ---------------------------------------------------------------------------
+// Setup kernels for one system and one k (warp per target):
+//   mode 0: S_k (Eq. 7);  mode 1: H_k at A = 0 = H0_k + (eps_I + eps_J)/2 S_k
+// written densely into out (Np x Np, zeros elsewhere set by the caller), and
+// the Mulliken partial sum per target of a density set D (all k, weighted).
+// ---------------------------------------------------------------------------
+__global__ void k_bloch_setup(const DevSys* __restrict__ sysv, int s_idx, int k, int mode,
+                              const double* __restrict__ eps, double2* out) {
+  const int tg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const DevSys& S = sysv[s_idx];
+  if (tg >= S.n_tgt) return;
+  const int I = S.tgt_I[tg], J = S.tgt_J[tg];
+  const int oi = S.orb_off[I], ni = S.orb_off[I + 1] - oi;
+  const int oj = S.orb_off[J], nj = S.orb_off[J + 1] - oj;
+  const double beta = mode == 1 ? 0.5 * (eps[I] + eps[J]) : 0.0;
+  for (int e = lane; e < ni * nj; e += 32) {
+    const int a = e / nj, b = e - a * nj;
+    double xr = 0.0, xi = 0.0;
+    for (int g = S.tgt_img0[tg]; g < S.tgt_img0[tg + 1]; ++g) {
+      const int blk = S.img_blk[g];
+      const long long off = S.blk_off[blk] + e;
+      const double v = mode == 1 ? S.h0[off] + beta * S.s[off] : S.s[off];
+      const double2 ph = S.phase[(long long)k * S.n_blk + blk];
+      xr += ph.x * v;
+      xi += ph.y * v;
+    }
+    out[(long long)(oi + a) * S.Np + (oj + b)] = make_double2(xr, xi);
+  }
+}
+
+__global__ void k_mulliken_setup(const DevSys* __restrict__ sysv, int s_idx, const double2* __restrict__ D,
+                                 double* part) {
+  const int tg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const DevSys& S = sysv[s_idx];
+  if (tg >= S.n_tgt) return;
+  const int I = S.tgt_I[tg], J = S.tgt_J[tg];
+  const int oi = S.orb_off[I], ni = S.orb_off[I + 1] - oi;
+  const int oj = S.orb_off[J], nj = S.orb_off[J + 1] - oj;
+  const long long NN = (long long)S.Np * S.Np;
+  double acc = 0.0;
+  for (int e = lane; e < ni * nj; e += 32) {
+    const int a = e / nj, b = e - a * nj;
+    const long long idx = (long long)(oi + a) * S.Np + (oj + b);
+    for (int k = 0; k < S.nk; ++k) {
+      const double2 d = D[k * NN + idx];
+      double l = 0.0;
+      for (int g = S.tgt_img0[tg]; g < S.tgt_img0[tg + 1]; ++g) {
+        const int blk = S.img_blk[g];
+        const double2 ph = S.phase[(long long)k * S.n_blk + blk];
+        l += S.s[S.blk_off[blk] + e] * (d.x * ph.x + d.y * ph.y);
+      }
+      acc += S.wk[k] * l;
+    }
+  }
+  acc = warp_sum(acc);
+  if (lane == 0) part[tg] = acc;
+}
+
+void launch_bloch_setup(const DevSys* sys, int s_idx, int n_tgt, int k, int mode, const double* eps,
+                        double2* out, cudaStream_t st) {
+  const int threads = 256;
+  const int blocks = (n_tgt * 32 + threads - 1) / threads;
+  k_bloch_setup<<<blocks, threads, 0, st>>>(sys, s_idx, k, mode, eps, out);
+}
+
+void launch_mulliken_setup(const DevSys* sys, int s_idx, int n_tgt, const double2* D, double* part,
+                           cudaStream_t st) {
+  const int threads = 256;
+  const int blocks = (n_tgt * 32 + threads - 1) / threads;
+  k_mulliken_setup<<<blocks, threads, 0, st>>>(sys, s_idx, D, part);
+}
+
+}  // namespace vgtb

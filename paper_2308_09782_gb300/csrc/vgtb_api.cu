@@ -1,0 +1,1225 @@
+// libvgtb host runtime: the C-ABI of include/vgtb.h.
+//
+// create():   validate the system, group its real-space blocks into targets
+//             (distinct atom pairs) with their images, tabulate the Bloch phases,
+//             build S_k (Eq. 7) and S_k^-1 (cuSOLVER Cholesky), and either the SCC
+//             ground state (cuSOLVER generalized eigensolver + Anderson-mixed
+//             charges, Sec. 3.1) or wait for a user density.
+// propagate(): enqueue the step  obs -> scc -> phase -> product 1 -> product 2
+//             -> leapfrog  for all trajectories and k-points together, captured
+//             into a CUDA graph of `graph_steps` steps and replayed; a device step
+//             counter lets every replay run the same graph.
+#include <cuda_runtime.h>
+#include <cusolverDn.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/vgtb.h"
+#include "vgtb_internal.h"
+#include "vgtb_tc.h"
+
+using namespace vgtb;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct HostSys {
+  int N = 0, Np = 0, nat = 0, nk = 0, n_blk = 0, n_tgt = 0, nocc = 0;
+  double omega = 0, nel = 0, dt = 0;
+  std::vector<int> orb_off;
+  std::vector<double> z, gamma;
+  std::vector<int> tgt_I, tgt_J, tgt_img0, img_blk, atom_tgt0;
+  std::vector<long long> blk_off;
+  std::vector<double> wk;
+  // device
+  double2* Sinv = nullptr;
+  double2* D0 = nullptr;
+  double2* R0 = nullptr;
+  double* dq0 = nullptr;
+  double* eps0 = nullptr;
+  __nv_bfloat16* Sinv_p = nullptr;
+  __nv_bfloat16* D0_p = nullptr;
+  std::vector<double> dq0_h, eps0_h;
+  bool density_set = false;
+  std::vector<int> trajs;  // trajectories of this system
+  std::vector<char> k_set;  // which k-points received a user density
+};
+
+struct HostTraj {
+  int sys = 0, item0 = 0;
+  int n_times = 0;
+  double* A = nullptr;
+  double* J = nullptr;
+  double* E = nullptr;
+  double* q = nullptr;
+  double* dq = nullptr;
+  double* eps = nullptr;
+  double* part = nullptr;
+  int* status = nullptr;
+};
+
+}  // namespace
+
+struct vgtb_ctx {
+  vgtb_options opt{};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string err;
+  std::vector<void*> allocs;
+  std::vector<HostSys> sys;
+  std::vector<HostTraj> trj;
+  std::vector<DevItem> items_h;
+  DevSys* d_sys = nullptr;
+  DevTraj* d_trj = nullptr;
+  DevItem* d_items = nullptr;
+  int* d_wpre = nullptr;
+  int total_warps = 0;
+  int max_nat = 0, max_Np = 0;
+  int* d_step = nullptr;
+  int* d_counter = nullptr;
+  int n_done = 0;
+  bool split = false, delta = false;
+  // FP64 GEMM / leap work lists
+  GemmF64Item* d_g1 = nullptr;
+  GemmF64Item* d_g2 = nullptr;
+  LeapItem* d_leap = nullptr;
+  int n_items = 0;
+  // tcgen05 plans
+  TcPlan* tc1 = nullptr;
+  TcPlan* tc2 = nullptr;
+  // graph
+  cudaGraphExec_t graph = nullptr;
+  int graph_steps = 0;
+  bool graph_profiled = false;
+  // profiling
+  bool profile = false;
+  std::vector<cudaEvent_t> ev;
+  long long prof_launch[VGTB_K_COUNT] = {0};
+  double prof_ms[VGTB_K_COUNT] = {0};
+  cusolverDnHandle_t solver = nullptr;
+};
+
+namespace {
+
+int fail(vgtb_ctx* ctx, int code, const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (ctx)
+    ctx->err = buf;
+  else
+    g_create_error = buf;
+  return code;
+}
+
+#define CK(x)                                                                                \
+  do {                                                                                       \
+    cudaError_t e_ = (x);                                                                    \
+    if (e_ != cudaSuccess) {                                                                 \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? VGTB_E_NOMEM : VGTB_E_CUDA,         \
+                  "%s failed: %s (%s:%d)", #x, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    }                                                                                        \
+  } while (0)
+
+#define CKS(x)                                                                          \
+  do {                                                                                  \
+    cusolverStatus_t s_ = (x);                                                          \
+    if (s_ != CUSOLVER_STATUS_SUCCESS)                                                  \
+      return fail(ctx, VGTB_E_CUDA, "%s failed: cusolver status %d", #x, (int)s_);      \
+  } while (0)
+
+#define TRY(x)            \
+  do {                    \
+    int r_ = (x);         \
+    if (r_ != VGTB_OK) return r_; \
+  } while (0)
+
+template <class T>
+int dalloc(vgtb_ctx* ctx, T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) return VGTB_OK;
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+  if (e != cudaSuccess)
+    return fail(ctx, VGTB_E_NOMEM, "cudaMalloc of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
+  ctx->allocs.push_back(q);
+  e = cudaMemsetAsync(q, 0, count * sizeof(T), ctx->stream);
+  if (e != cudaSuccess) return fail(ctx, VGTB_E_CUDA, "cudaMemset failed: %s", cudaGetErrorString(e));
+  *p = (T*)q;
+  return VGTB_OK;
+}
+
+template <class T>
+int upload(vgtb_ctx* ctx, T** p, const T* src, size_t count) {
+  TRY(dalloc(ctx, p, count));
+  if (count) CK(cudaMemcpyAsync(*p, src, count * sizeof(T), cudaMemcpyHostToDevice, ctx->stream));
+  return VGTB_OK;
+}
+
+bool finite_all(const double* p, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(p[i])) return false;
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// validation and target grouping of one system
+// ---------------------------------------------------------------------------
+int prepare_system(vgtb_ctx* ctx, int si, const vgtb_system& s, HostSys& h, DevSys& d, bool need_ground) {
+  if (s.n_atoms < 1 || !s.pos || !s.orb_offset || !s.z_ref || s.n_blocks < 1 || !s.blk_ijl || !s.h0 || !s.s ||
+      !s.ds || !s.gamma || s.n_k < 1 || !s.kpt || !s.wk)
+    return fail(ctx, VGTB_E_INVALID, "system %d: missing array or empty dimension", si);
+  if (!(s.dt > 0.0) || !std::isfinite(s.dt)) return fail(ctx, VGTB_E_INVALID, "system %d: dt must be > 0", si);
+  h.nat = s.n_atoms;
+  h.orb_off.assign(s.orb_offset, s.orb_offset + s.n_atoms + 1);
+  if (h.orb_off[0] != 0) return fail(ctx, VGTB_E_INVALID, "system %d: orb_offset[0] must be 0", si);
+  for (int i = 0; i < s.n_atoms; ++i)
+    if (h.orb_off[i + 1] <= h.orb_off[i])
+      return fail(ctx, VGTB_E_INVALID, "system %d: orb_offset must increase strictly (atom %d)", si, i);
+  h.N = h.orb_off[s.n_atoms];
+  h.Np = (h.N + 127) / 128 * 128;
+  h.nel = s.n_electrons;
+  if (!(s.n_electrons > 0.0) || s.n_electrons > 2.0 * h.N || !std::isfinite(s.n_electrons))
+    return fail(ctx, VGTB_E_INVALID, "system %d: n_electrons must be in (0, 2N]", si);
+  if (need_ground) {
+    const double half = 0.5 * s.n_electrons;
+    if (std::fabs(half - std::round(half)) > 1e-12)
+      return fail(ctx, VGTB_E_INVALID, "system %d: ground state needs an even electron count", si);
+    h.nocc = (int)std::llround(half);
+  }
+  h.dt = s.dt;
+  const double* L = s.lattice;
+  const double det = L[0] * (L[4] * L[8] - L[5] * L[7]) - L[1] * (L[3] * L[8] - L[5] * L[6]) +
+                     L[2] * (L[3] * L[7] - L[4] * L[6]);
+  h.omega = std::fabs(det);
+  if (!(h.omega > 0.0) || !finite_all(L, 9)) return fail(ctx, VGTB_E_INVALID, "system %d: singular lattice", si);
+  if (!finite_all(s.pos, 3 * (size_t)s.n_atoms) || !finite_all(s.z_ref, s.n_atoms))
+    return fail(ctx, VGTB_E_INVALID, "system %d: non-finite positions or Z", si);
+  // blocks
+  h.n_blk = s.n_blocks;
+  h.blk_off.resize(s.n_blocks);
+  long long tot = 0;
+  std::map<std::tuple<int, int, int, int, int>, int> key;
+  for (int b = 0; b < s.n_blocks; ++b) {
+    const int* r = s.blk_ijl + 5 * b;
+    if (r[0] < 0 || r[0] >= s.n_atoms || r[1] < 0 || r[1] >= s.n_atoms)
+      return fail(ctx, VGTB_E_INVALID, "system %d: block %d atom index out of range", si, b);
+    h.blk_off[b] = tot;
+    tot += (long long)(h.orb_off[r[0] + 1] - h.orb_off[r[0]]) * (h.orb_off[r[1] + 1] - h.orb_off[r[1]]);
+    if (!key.emplace(std::make_tuple(r[0], r[1], r[2], r[3], r[4]), b).second)
+      return fail(ctx, VGTB_E_INVALID, "system %d: duplicate block (%d,%d,%d,%d,%d)", si, r[0], r[1], r[2], r[3], r[4]);
+  }
+  if (!finite_all(s.h0, tot) || !finite_all(s.s, tot) || !finite_all(s.ds, 3 * tot))
+    return fail(ctx, VGTB_E_INVALID, "system %d: non-finite block values", si);
+  // mirror blocks: (J, I, -n) with transposed S/H0 and negated transposed dS
+  double smax = 0.0;
+  for (long long i = 0; i < tot; ++i) smax = std::max(smax, std::fabs(s.s[i]) + std::fabs(s.h0[i]));
+  for (int b = 0; b < s.n_blocks; ++b) {
+    const int* r = s.blk_ijl + 5 * b;
+    auto it = key.find(std::make_tuple(r[1], r[0], -r[2], -r[3], -r[4]));
+    if (it == key.end())
+      return fail(ctx, VGTB_E_INVALID, "system %d: block (%d,%d,%d,%d,%d) has no mirror block", si, r[0], r[1], r[2],
+                  r[3], r[4]);
+    const int m = it->second;
+    const int ni = h.orb_off[r[0] + 1] - h.orb_off[r[0]], nj = h.orb_off[r[1] + 1] - h.orb_off[r[1]];
+    for (int a = 0; a < ni; ++a)
+      for (int c = 0; c < nj; ++c) {
+        const long long e1 = h.blk_off[b] + a * nj + c, e2 = h.blk_off[m] + c * ni + a;
+        const double tol = 1e-12 * std::max(1.0, smax);
+        bool bad = std::fabs(s.s[e1] - s.s[e2]) > tol || std::fabs(s.h0[e1] - s.h0[e2]) > tol;
+        for (int x = 0; x < 3; ++x) bad |= std::fabs(s.ds[x * tot + e1] + s.ds[x * tot + e2]) > tol;
+        if (bad)
+          return fail(ctx, VGTB_E_INVALID, "system %d: block %d and its mirror are not Hermitian partners", si, b);
+      }
+  }
+  // gamma
+  h.gamma.assign(s.gamma, s.gamma + (size_t)s.n_atoms * s.n_atoms);
+  if (!finite_all(h.gamma.data(), h.gamma.size())) return fail(ctx, VGTB_E_INVALID, "system %d: non-finite gamma", si);
+  double gmax = 0.0;
+  for (double g : h.gamma) gmax = std::max(gmax, std::fabs(g));
+  for (int i = 0; i < s.n_atoms; ++i)
+    for (int j = 0; j < i; ++j)
+      if (std::fabs(h.gamma[(size_t)i * s.n_atoms + j] - h.gamma[(size_t)j * s.n_atoms + i]) > 1e-12 * std::max(1.0, gmax))
+        return fail(ctx, VGTB_E_INVALID, "system %d: gamma is not symmetric", si);
+  // k points
+  h.nk = s.n_k;
+  if (!finite_all(s.kpt, 3 * (size_t)s.n_k) || !finite_all(s.wk, s.n_k))
+    return fail(ctx, VGTB_E_INVALID, "system %d: non-finite k-points", si);
+  h.wk.assign(s.wk, s.wk + s.n_k);
+  double wsum = 0.0;
+  for (double w : h.wk) wsum += w;
+  if (std::fabs(wsum - 1.0) > 1e-10) return fail(ctx, VGTB_E_INVALID, "system %d: k weights sum to %.15g", si, wsum);
+  h.z.assign(s.z_ref, s.z_ref + s.n_atoms);
+  // targets: distinct (I, J) sorted by I then J; images in (n1, n2, n3) order
+  std::vector<int> order(s.n_blocks);
+  for (int b = 0; b < s.n_blocks; ++b) order[b] = b;
+  std::sort(order.begin(), order.end(), [&](int a, int b) {
+    const int* x = s.blk_ijl + 5 * a;
+    const int* y = s.blk_ijl + 5 * b;
+    return std::lexicographical_compare(x, x + 5, y, y + 5);
+  });
+  h.tgt_I.clear();
+  h.tgt_J.clear();
+  h.tgt_img0.clear();
+  h.img_blk.clear();
+  for (int idx = 0; idx < s.n_blocks; ++idx) {
+    const int b = order[idx];
+    const int* r = s.blk_ijl + 5 * b;
+    if (h.tgt_I.empty() || h.tgt_I.back() != r[0] || h.tgt_J.back() != r[1]) {
+      h.tgt_I.push_back(r[0]);
+      h.tgt_J.push_back(r[1]);
+      h.tgt_img0.push_back((int)h.img_blk.size());
+    }
+    h.img_blk.push_back(b);
+  }
+  h.tgt_img0.push_back((int)h.img_blk.size());
+  h.n_tgt = (int)h.tgt_I.size();
+  h.atom_tgt0.assign(s.n_atoms + 1, 0);
+  for (int t = 0; t < h.n_tgt; ++t) h.atom_tgt0[h.tgt_I[t] + 1]++;
+  for (int i = 0; i < s.n_atoms; ++i) h.atom_tgt0[i + 1] += h.atom_tgt0[i];
+  // phases e^{-i 2 pi k.n}
+  std::vector<double2> ph((size_t)s.n_k * s.n_blocks);
+  for (int k = 0; k < s.n_k; ++k)
+    for (int b = 0; b < s.n_blocks; ++b) {
+      const int* r = s.blk_ijl + 5 * b;
+      const double th = 2.0 * M_PI * (s.kpt[3 * k] * r[2] + s.kpt[3 * k + 1] * r[3] + s.kpt[3 * k + 2] * r[4]);
+      ph[(size_t)k * s.n_blocks + b] = make_double2(std::cos(th), -std::sin(th));
+    }
+  // upload
+  memset(&d, 0, sizeof(d));
+  d.N = h.N;
+  d.Np = h.Np;
+  d.nat = h.nat;
+  d.nk = h.nk;
+  d.n_tgt = h.n_tgt;
+  d.n_blk = h.n_blk;
+  d.omega = h.omega;
+  d.nel = h.nel;
+  d.dt = h.dt;
+  int* pi;
+  double* pd;
+  long long* pl;
+  double2* pz;
+  TRY(upload(ctx, &pi, h.orb_off.data(), h.orb_off.size()));
+  d.orb_off = pi;
+  TRY(upload(ctx, &pd, h.z.data(), h.z.size()));
+  d.z = pd;
+  TRY(upload(ctx, &pd, h.gamma.data(), h.gamma.size()));
+  d.gamma = pd;
+  TRY(upload(ctx, &pi, h.tgt_I.data(), h.tgt_I.size()));
+  d.tgt_I = pi;
+  TRY(upload(ctx, &pi, h.tgt_J.data(), h.tgt_J.size()));
+  d.tgt_J = pi;
+  TRY(upload(ctx, &pi, h.tgt_img0.data(), h.tgt_img0.size()));
+  d.tgt_img0 = pi;
+  TRY(upload(ctx, &pi, h.img_blk.data(), h.img_blk.size()));
+  d.img_blk = pi;
+  TRY(upload(ctx, &pl, h.blk_off.data(), h.blk_off.size()));
+  d.blk_off = pl;
+  TRY(upload(ctx, &pd, s.h0, (size_t)tot));
+  d.h0 = pd;
+  TRY(upload(ctx, &pd, s.s, (size_t)tot));
+  d.s = pd;
+  TRY(upload(ctx, &pd, s.ds, 3 * (size_t)tot));
+  d.ds = pd;
+  d.ds_stride = tot;
+  TRY(upload(ctx, &pz, ph.data(), ph.size()));
+  d.phase = pz;
+  TRY(upload(ctx, &pd, h.wk.data(), h.wk.size()));
+  d.wk = pd;
+  TRY(upload(ctx, &pi, h.atom_tgt0.data(), h.atom_tgt0.size()));
+  d.atom_tgt0 = pi;
+  const size_t NN = (size_t)h.Np * h.Np;
+  TRY(dalloc(ctx, &h.Sinv, NN * h.nk));
+  TRY(dalloc(ctx, &h.D0, NN * h.nk));
+  TRY(dalloc(ctx, &h.dq0, h.nat));
+  TRY(dalloc(ctx, &h.eps0, h.nat));
+  if (ctx->delta) TRY(dalloc(ctx, &h.R0, NN * h.nk));
+  if (ctx->split) {
+    TRY(dalloc(ctx, &h.Sinv_p, 4 * NN * h.nk));
+    TRY(dalloc(ctx, &h.D0_p, 4 * NN * h.nk));
+  }
+  d.Sinv = h.Sinv;
+  d.D0 = h.D0;
+  d.R0 = h.R0;
+  d.dq0 = h.dq0;
+  d.eps0 = h.eps0;
+  d.Sinv_p = h.Sinv_p;
+  d.D0_p = h.D0_p;
+  return VGTB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// S_k^-1 by Cholesky (cuSOLVER).  A row-major Hermitian buffer read as
+// column-major is conj(S); potrf/potri of conj(S) give conj(S^-1), whose
+// row-major reading is S^-1 again (upper triangle valid, then mirrored).
+// ---------------------------------------------------------------------------
+int build_sinv(vgtb_ctx* ctx, int si) {
+  HostSys& h = ctx->sys[si];
+  const size_t NN = (size_t)h.Np * h.Np;
+  int* info = nullptr;
+  TRY(dalloc(ctx, &info, 1));
+  for (int k = 0; k < h.nk; ++k) {
+    double2* S = h.Sinv + k * NN;
+    launch_bloch_setup(ctx->d_sys, si, h.n_tgt, k, 0, nullptr, S, ctx->stream);
+    CK(cudaGetLastError());
+    int lw = 0;
+    CKS(cusolverDnZpotrf_bufferSize(ctx->solver, CUBLAS_FILL_MODE_LOWER, h.N, (cuDoubleComplex*)S, h.Np, &lw));
+    int lw2 = 0;
+    CKS(cusolverDnZpotri_bufferSize(ctx->solver, CUBLAS_FILL_MODE_LOWER, h.N, (cuDoubleComplex*)S, h.Np, &lw2));
+    lw = std::max(lw, lw2);
+    cuDoubleComplex* work = nullptr;
+    CK(cudaMalloc(&work, sizeof(cuDoubleComplex) * std::max(lw, 1)));
+    cusolverStatus_t st = cusolverDnZpotrf(ctx->solver, CUBLAS_FILL_MODE_LOWER, h.N, (cuDoubleComplex*)S, h.Np, work, lw, info);
+    int hinfo = 0;
+    cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    cudaStreamSynchronize(ctx->stream);
+    if (st != CUSOLVER_STATUS_SUCCESS || hinfo != 0) {
+      cudaFree(work);
+      if (hinfo > 0) return fail(ctx, VGTB_E_NOT_PD, "system %d: S_k at k=%d is not positive definite (minor %d)", si, k, hinfo);
+      return fail(ctx, VGTB_E_CUDA, "cusolverDnZpotrf failed: status %d info %d", (int)st, hinfo);
+    }
+    st = cusolverDnZpotri(ctx->solver, CUBLAS_FILL_MODE_LOWER, h.N, (cuDoubleComplex*)S, h.Np, work, lw, info);
+    cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(work);
+    if (st != CUSOLVER_STATUS_SUCCESS || hinfo != 0)
+      return fail(ctx, VGTB_E_CUDA, "cusolverDnZpotri failed: status %d info %d", (int)st, hinfo);
+    // column-major lower = row-major upper is valid; mirror it
+    launch_fill_hermitian_lower(S, h.N, h.Np, ctx->stream);
+    CK(cudaGetLastError());
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  return VGTB_OK;
+}
+
+// charges of a density set D (nk x Np^2) of system si: q_I on the host
+int host_charges(vgtb_ctx* ctx, int si, const double2* D, std::vector<double>& q) {
+  HostSys& h = ctx->sys[si];
+  double* part = nullptr;
+  TRY(dalloc(ctx, &part, h.n_tgt));
+  launch_mulliken_setup(ctx->d_sys, si, h.n_tgt, D, part, ctx->stream);
+  CK(cudaGetLastError());
+  std::vector<double> p(h.n_tgt);
+  CK(cudaMemcpyAsync(p.data(), part, sizeof(double) * h.n_tgt, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  q.assign(h.nat, 0.0);
+  for (int i = 0; i < h.nat; ++i)
+    for (int t = h.atom_tgt0[i]; t < h.atom_tgt0[i + 1]; ++t) q[i] += p[t];
+  return VGTB_OK;
+}
+
+void gamma_mul(const HostSys& h, const std::vector<double>& dq, std::vector<double>& eps) {
+  eps.assign(h.nat, 0.0);
+  for (int i = 0; i < h.nat; ++i) {
+    double e = 0.0;
+    for (int j = 0; j < h.nat; ++j) e += h.gamma[(size_t)i * h.nat + j] * dq[j];
+    eps[i] = e;
+  }
+}
+
+// small dense solve (Gaussian elimination with partial pivoting), n <= 16
+bool solve_small(std::vector<double> a, std::vector<double>& b, int n) {
+  for (int c = 0; c < n; ++c) {
+    int p = c;
+    for (int r = c + 1; r < n; ++r)
+      if (std::fabs(a[r * n + c]) > std::fabs(a[p * n + c])) p = r;
+    if (std::fabs(a[p * n + c]) < 1e-300) return false;
+    for (int j = 0; j < n; ++j) std::swap(a[c * n + j], a[p * n + j]);
+    std::swap(b[c], b[p]);
+    for (int r = 0; r < n; ++r) {
+      if (r == c) continue;
+      const double f = a[r * n + c] / a[c * n + c];
+      for (int j = 0; j < n; ++j) a[r * n + j] -= f * a[c * n + j];
+      b[r] -= f * b[c];
+    }
+  }
+  for (int c = 0; c < n; ++c) b[c] /= a[c * n + c];
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// SCC ground state (Sec. 3.1): diagonalise H_k[dq] C = S_k C e at every k,
+// occupy the lowest N_el/2 states twice, recompute dq; Pulay (DIIS) mixing
+// of dq on the host until max |dq_out - dq_in| < tol.
+// ---------------------------------------------------------------------------
+int ground_state(vgtb_ctx* ctx, int si) {
+  HostSys& h = ctx->sys[si];
+  const size_t NN = (size_t)h.Np * h.Np;
+  double2 *Hb = nullptr, *Sb = nullptr, *Vt = nullptr;
+  double* w = nullptr;
+  double* eps_d = nullptr;
+  int* info = nullptr;
+  TRY(dalloc(ctx, &Hb, NN));
+  TRY(dalloc(ctx, &Sb, NN));
+  TRY(dalloc(ctx, &Vt, (size_t)h.N * std::max(h.nocc, 1)));
+  TRY(dalloc(ctx, &w, h.Np));
+  TRY(dalloc(ctx, &eps_d, h.nat));
+  TRY(dalloc(ctx, &info, 1));
+  GemmF64Item gi{};
+  GemmF64Item* d_gi = nullptr;
+  TRY(dalloc(ctx, &d_gi, 1));
+  int lw = 0;
+  CKS(cusolverDnZhegvd_bufferSize(ctx->solver, CUSOLVER_EIG_TYPE_1, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER,
+                                  h.N, (cuDoubleComplex*)Hb, h.Np, (cuDoubleComplex*)Sb, h.Np, w, &lw));
+  cuDoubleComplex* work = nullptr;
+  TRY(dalloc(ctx, &work, std::max(lw, 1)));
+  const double tol = ctx->opt.scc_tol > 0 ? ctx->opt.scc_tol : 1e-11;
+  const int max_it = ctx->opt.scc_max_iter > 0 ? ctx->opt.scc_max_iter : 200;
+  const double mix = 0.2;
+  const int hist = 8;
+  std::vector<double> dq(h.nat, 0.0), eps, q, res;
+  std::vector<std::vector<double>> xs, fs;
+  bool any_gamma = false;
+  for (double g : h.gamma) any_gamma |= (g != 0.0);
+  std::vector<double> ev(h.N);
+  for (int it = 1; it <= max_it; ++it) {
+    gamma_mul(h, dq, eps);
+    CK(cudaMemcpyAsync(eps_d, eps.data(), sizeof(double) * h.nat, cudaMemcpyHostToDevice, ctx->stream));
+    for (int k = 0; k < h.nk; ++k) {
+      CK(cudaMemsetAsync(Hb, 0, NN * sizeof(double2), ctx->stream));
+      CK(cudaMemsetAsync(Sb, 0, NN * sizeof(double2), ctx->stream));
+      launch_bloch_setup(ctx->d_sys, si, h.n_tgt, k, 1, eps_d, Hb, ctx->stream);
+      launch_bloch_setup(ctx->d_sys, si, h.n_tgt, k, 0, nullptr, Sb, ctx->stream);
+      CK(cudaGetLastError());
+      CKS(cusolverDnZhegvd(ctx->solver, CUSOLVER_EIG_TYPE_1, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, h.N,
+                           (cuDoubleComplex*)Hb, h.Np, (cuDoubleComplex*)Sb, h.Np, w, work, lw, info));
+      int hinfo = 0;
+      CK(cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+      CK(cudaMemcpyAsync(ev.data(), w, sizeof(double) * h.N, cudaMemcpyDeviceToHost, ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+      if (hinfo > h.N) return fail(ctx, VGTB_E_NOT_PD, "system %d: S_k at k=%d is not positive definite", si, k);
+      if (hinfo != 0) return fail(ctx, VGTB_E_CUDA, "cusolverDnZhegvd info %d", hinfo);
+      if (h.nocc < h.N && ev[h.nocc] - ev[h.nocc - 1] < 1e-8)
+        return fail(ctx, VGTB_E_NO_GAP, "system %d: no gap at N_el/2 at k=%d (%.3e Ha)", si, k, ev[h.nocc] - ev[h.nocc - 1]);
+      // D_k = 2 V V^dagger over the occupied eigenvectors
+      launch_vt_from_evecs(Hb, Vt, h.N, h.nocc, h.Np, ctx->stream);
+      gi.A[0] = Vt;
+      gi.R[0] = Vt;
+      gi.a_par[0] = 0;
+      gi.C = h.D0 + k * NN;
+      gi.K[0] = h.nocc;
+      gi.lda[0] = gi.ldr[0] = h.nocc;
+      gi.nseg = 1;
+      gi.M = gi.N = h.N;
+      gi.ldc = h.Np;
+      CK(cudaMemcpyAsync(d_gi, &gi, sizeof(gi), cudaMemcpyHostToDevice, ctx->stream));
+      launch_gemm_f64(d_gi, 1, h.N, h.N, nullptr, ctx->stream);
+      launch_scale(h.D0 + k * NN, (long long)NN, 2.0, ctx->stream);
+      CK(cudaGetLastError());
+    }
+    TRY(host_charges(ctx, si, h.D0, q));
+    res.assign(h.nat, 0.0);
+    double rmax = 0.0;
+    for (int i = 0; i < h.nat; ++i) {
+      res[i] = (q[i] - h.z[i]) - dq[i];
+      rmax = std::max(rmax, std::fabs(res[i]));
+    }
+    if (rmax < tol || !any_gamma) return VGTB_OK;
+    xs.push_back(dq);
+    fs.push_back(res);
+    if ((int)xs.size() > hist) {
+      xs.erase(xs.begin());
+      fs.erase(fs.begin());
+    }
+    const int m = (int)fs.size();
+    std::vector<double> nx(h.nat, 0.0);
+    if (m == 1) {
+      for (int i = 0; i < h.nat; ++i) nx[i] = dq[i] + mix * res[i];
+    } else {
+      // minimise |sum c_j f_j| with sum c_j = 1 (Lagrange system of size m+1)
+      std::vector<double> a((m + 1) * (m + 1), 0.0), b(m + 1, 0.0);
+      for (int r = 0; r < m; ++r)
+        for (int c = 0; c < m; ++c) {
+          double s = 0.0;
+          for (int i = 0; i < h.nat; ++i) s += fs[r][i] * fs[c][i];
+          a[r * (m + 1) + c] = s;
+        }
+      for (int r = 0; r < m; ++r) {
+        a[r * (m + 1) + m] = 1.0;
+        a[m * (m + 1) + r] = 1.0;
+      }
+      b[m] = 1.0;
+      if (!solve_small(a, b, m + 1)) {
+        for (int i = 0; i < h.nat; ++i) nx[i] = dq[i] + mix * res[i];
+      } else {
+        for (int j = 0; j < m; ++j)
+          for (int i = 0; i < h.nat; ++i) nx[i] += b[j] * (xs[j][i] + mix * fs[j][i]);
+      }
+    }
+    dq.swap(nx);
+  }
+  return fail(ctx, VGTB_E_NO_CONVERGE, "system %d: SCC ground state not converged in %d iterations", si, max_it);
+}
+
+// After D0 is set: charges of D0, eps0, R0 (delta forms), split pieces, and
+// every trajectory of the system back to step 0.
+int finish_density(vgtb_ctx* ctx, int si) {
+  HostSys& h = ctx->sys[si];
+  const size_t NN = (size_t)h.Np * h.Np;
+  for (int k = 0; k < h.nk; ++k) launch_hermitize(h.D0 + k * NN, h.N, h.Np, ctx->stream);
+  CK(cudaGetLastError());
+  std::vector<double> q;
+  TRY(host_charges(ctx, si, h.D0, q));
+  h.dq0_h.assign(h.nat, 0.0);
+  for (int i = 0; i < h.nat; ++i) h.dq0_h[i] = q[i] - h.z[i];
+  gamma_mul(h, h.dq0_h, h.eps0_h);
+  CK(cudaMemcpyAsync(h.dq0, h.dq0_h.data(), sizeof(double) * h.nat, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(h.eps0, h.eps0_h.data(), sizeof(double) * h.nat, cudaMemcpyHostToDevice, ctx->stream));
+  if (ctx->delta) {
+    // R0 = -i(S^-1 H_ref D0 - h.c.) with H_ref = H(A = 0, eps0), all in FP64
+    double2 *Hb = nullptr, *Wb = nullptr, *Xb = nullptr;
+    TRY(dalloc(ctx, &Hb, NN));
+    TRY(dalloc(ctx, &Wb, NN));
+    TRY(dalloc(ctx, &Xb, NN));
+    double* eps_d = h.eps0;
+    GemmF64Item g[2] = {};
+    GemmF64Item* dg = nullptr;
+    LeapItem li{};
+    LeapItem* dl = nullptr;
+    TRY(dalloc(ctx, &dg, 2));
+    TRY(dalloc(ctx, &dl, 1));
+    for (int k = 0; k < h.nk; ++k) {
+      CK(cudaMemsetAsync(Hb, 0, NN * sizeof(double2), ctx->stream));
+      launch_bloch_setup(ctx->d_sys, si, h.n_tgt, k, 1, eps_d, Hb, ctx->stream);
+      g[0] = GemmF64Item{};
+      g[0].A[0] = h.D0 + k * NN;
+      g[0].R[0] = Hb;
+      g[0].K[0] = h.Np;
+      g[0].lda[0] = g[0].ldr[0] = h.Np;
+      g[0].nseg = 1;
+      g[0].M = g[0].N = g[0].ldc = h.Np;
+      g[0].C = Wb;
+      g[1] = g[0];
+      g[1].A[0] = h.Sinv + k * NN;
+      g[1].R[0] = Wb;
+      g[1].C = Xb;
+      CK(cudaMemcpyAsync(dg, g, sizeof(g), cudaMemcpyHostToDevice, ctx->stream));
+      launch_gemm_f64(dg, 1, h.Np, h.Np, nullptr, ctx->stream);
+      launch_gemm_f64(dg + 1, 1, h.Np, h.Np, nullptr, ctx->stream);
+      li = LeapItem{};
+      li.X = Xb;
+      li.Np = h.Np;
+      li.mode = 1;
+      li.out = h.R0 + k * NN;
+      CK(cudaMemcpyAsync(dl, &li, sizeof(li), cudaMemcpyHostToDevice, ctx->stream));
+      launch_leap(dl, 1, h.Np, 0, nullptr, 0.0, nullptr, nullptr, ctx->stream);
+      CK(cudaGetLastError());
+      CK(cudaStreamSynchronize(ctx->stream));
+    }
+  }
+  if (ctx->split) {
+    for (int k = 0; k < h.nk; ++k) {
+      launch_split_planar(h.D0 + k * NN, h.D0_p + 4 * NN * k, h.N, h.Np, ctx->stream);
+      launch_split_planar(h.Sinv + k * NN, h.Sinv_p + 4 * NN * k, h.N, h.Np, ctx->stream);
+    }
+    CK(cudaGetLastError());
+  }
+  h.density_set = true;
+  CK(cudaStreamSynchronize(ctx->stream));
+  return VGTB_OK;
+}
+
+// Reset every trajectory to step 0 (D = D0, or dD = 0 in the delta forms).
+int reset_all(vgtb_ctx* ctx) {
+  for (auto& it : ctx->items_h) {
+    const HostSys& h = ctx->sys[it.sys];
+    const size_t NN = (size_t)h.Np * h.Np;
+    if (ctx->delta)
+      CK(cudaMemsetAsync(it.D[0], 0, NN * sizeof(double2), ctx->stream));
+    else
+      CK(cudaMemcpyAsync(it.D[0], h.D0 + it.k * NN, NN * sizeof(double2), cudaMemcpyDeviceToDevice, ctx->stream));
+    if (it.dD_p) CK(cudaMemsetAsync(it.dD_p, 0, 4 * NN * sizeof(__nv_bfloat16), ctx->stream));
+  }
+  for (auto& t : ctx->trj) CK(cudaMemsetAsync(t.status, 0, sizeof(int), ctx->stream));
+  CK(cudaMemsetAsync(ctx->d_step, 0, sizeof(int), ctx->stream));
+  CK(cudaMemsetAsync(ctx->d_counter, 0, sizeof(int), ctx->stream));
+  ctx->n_done = 0;
+  CK(cudaStreamSynchronize(ctx->stream));
+  return VGTB_OK;
+}
+
+int upload_traj_table(vgtb_ctx* ctx) {
+  std::vector<DevTraj> dt(ctx->trj.size());
+  for (size_t t = 0; t < ctx->trj.size(); ++t) {
+    const HostTraj& h = ctx->trj[t];
+    DevTraj& d = dt[t];
+    memset(&d, 0, sizeof(d));
+    d.sys = h.sys;
+    d.item0 = h.item0;
+    d.n_times = h.n_times;
+    d.A = h.A;
+    d.J = h.J;
+    d.E = h.E;
+    d.q = h.q;
+    d.dq = h.dq;
+    d.eps = h.eps;
+    d.part = h.part;
+    d.status = h.status;
+  }
+  CK(cudaMemcpyAsync(ctx->d_trj, dt.data(), sizeof(DevTraj) * dt.size(), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return VGTB_OK;
+}
+
+void drop_graph(vgtb_ctx* ctx) {
+  if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
+  ctx->graph = nullptr;
+}
+
+// ---------------------------------------------------------------------------
+// one step for every trajectory; ev != nullptr records 7 timing events
+// ---------------------------------------------------------------------------
+int enqueue_step(vgtb_ctx* ctx, cudaEvent_t* ev) {
+  cudaStream_t st = ctx->stream;
+  const int nt = (int)ctx->trj.size();
+  const int stride = ctx->opt.obs_stride > 0 ? ctx->opt.obs_stride : 1;
+  if (ev) CK(cudaEventRecord(ev[0], st));
+  launch_obs(ctx->d_sys, ctx->d_trj, ctx->d_items, ctx->d_wpre, nt, ctx->total_warps, ctx->d_step, ctx->delta ? 1 : 0,
+             -1, st);
+  if (ev) CK(cudaEventRecord(ev[1], st));
+  launch_scc(ctx->d_sys, ctx->d_trj, nt, ctx->d_step, stride, -1, 1, ctx->max_nat, st);
+  if (ev) CK(cudaEventRecord(ev[2], st));
+  const int mode = ctx->split ? PH_SPLIT : (ctx->delta ? PH_FP64_DELTA : PH_FP64_PLAIN);
+  launch_phase(ctx->d_sys, ctx->d_trj, ctx->d_items, ctx->d_wpre, nt, ctx->total_warps, ctx->d_step, mode, -1, st);
+  if (ev) CK(cudaEventRecord(ev[3], st));
+  if (ctx->split) {
+    TRY(tc_launch(ctx->tc1, st) == 0 ? VGTB_OK : fail(ctx, VGTB_E_CUDA, "tcgen05 product 1 launch failed"));
+    if (ev) CK(cudaEventRecord(ev[4], st));
+    TRY(tc_launch(ctx->tc2, st) == 0 ? VGTB_OK : fail(ctx, VGTB_E_CUDA, "tcgen05 product 2 launch failed"));
+  } else {
+    launch_gemm_f64(ctx->d_g1, ctx->n_items, ctx->max_Np, ctx->max_Np, ctx->d_step, st);
+    if (ev) CK(cudaEventRecord(ev[4], st));
+    launch_gemm_f64(ctx->d_g2, ctx->n_items, ctx->max_Np, ctx->max_Np, ctx->d_step, st);
+  }
+  if (ev) CK(cudaEventRecord(ev[5], st));
+  launch_leap(ctx->d_leap, ctx->n_items, ctx->max_Np, ctx->split ? 1 : 0, ctx->d_step, ctx->sys[0].dt,
+              ctx->d_counter, ctx->d_step, st);
+  if (ev) CK(cudaEventRecord(ev[6], st));
+  CK(cudaGetLastError());
+  return VGTB_OK;
+}
+
+int accumulate_events(vgtb_ctx* ctx, int nsteps) {
+  CK(cudaEventSynchronize(ctx->ev[7 * nsteps - 1]));
+  for (int s = 0; s < nsteps; ++s) {
+    cudaEvent_t* e = &ctx->ev[7 * s];
+    for (int c = 0; c < VGTB_K_COUNT; ++c) {
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, e[c], e[c + 1]));
+      ctx->prof_ms[c] += ms;
+      ctx->prof_launch[c] += 1;
+    }
+  }
+  return VGTB_OK;
+}
+
+int ensure_events(vgtb_ctx* ctx, int nsteps) {
+  while ((int)ctx->ev.size() < 7 * nsteps) {
+    cudaEvent_t e;
+    CK(cudaEventCreate(&e));
+    ctx->ev.push_back(e);
+  }
+  return VGTB_OK;
+}
+
+int build_graph(vgtb_ctx* ctx, int G) {
+  drop_graph(ctx);
+  if (ctx->profile) TRY(ensure_events(ctx, G));
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+  int rc = VGTB_OK;
+  for (int s = 0; s < G && rc == VGTB_OK; ++s) rc = enqueue_step(ctx, ctx->profile ? &ctx->ev[7 * s] : nullptr);
+  cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+  if (rc != VGTB_OK) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) return fail(ctx, VGTB_E_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&ctx->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(ctx, VGTB_E_CUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
+  ctx->graph_steps = G;
+  ctx->graph_profiled = ctx->profile;
+  return VGTB_OK;
+}
+
+int check_status(vgtb_ctx* ctx) {
+  for (size_t t = 0; t < ctx->trj.size(); ++t) {
+    int st = 0;
+    CK(cudaMemcpyAsync(&st, ctx->trj[t].status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (st & ST_TIMEOUT) return fail(ctx, VGTB_E_TIMEOUT, "trajectory %zu: a bounded device wait expired", t);
+    if (st & ST_NONFINITE) return fail(ctx, VGTB_E_UNSTABLE, "trajectory %zu: non-finite observables", t);
+    if (st & ST_DRIFT) return fail(ctx, VGTB_E_UNSTABLE, "trajectory %zu: electron count drifted", t);
+  }
+  const int tc = tc_status(ctx->tc1, ctx->stream) | tc_status(ctx->tc2, ctx->stream);
+  if (tc) return fail(ctx, VGTB_E_TIMEOUT, "tcgen05 product reported status %d (bounded wait expired)", tc);
+  return VGTB_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C-ABI
+// ===========================================================================
+extern "C" {
+
+void vgtb_default_options(vgtb_options* opt) {
+  if (!opt) return;
+  memset(opt, 0, sizeof(*opt));
+  opt->precision = VGTB_FP64;
+  opt->init = VGTB_INIT_GROUND;
+  opt->obs_stride = 1;
+  opt->graph_steps = 32;
+  opt->timeout_ns = 2000000000LL;
+  opt->scc_tol = 1e-11;
+  opt->scc_max_iter = 200;
+}
+
+int vgtb_create(vgtb_ctx** out, const vgtb_system* sys, const vgtb_options* opt) {
+  const int zero = 0;
+  return vgtb_create_batch(out, 1, sys, 1, &zero, opt);
+}
+
+int vgtb_create_batch(vgtb_ctx** out, int n_sys, const vgtb_system* sys, int n_traj, const int* traj_sys,
+                      const vgtb_options* opt) {
+  if (!out) return fail(nullptr, VGTB_E_INVALID, "out is NULL");
+  *out = nullptr;
+  if (n_sys < 1 || !sys || n_traj < 1 || !traj_sys) return fail(nullptr, VGTB_E_INVALID, "empty batch");
+  vgtb_ctx* ctx = new vgtb_ctx();
+  vgtb_default_options(&ctx->opt);
+  if (opt) ctx->opt = *opt;
+  if (ctx->opt.obs_stride <= 0) ctx->opt.obs_stride = 1;
+  if (ctx->opt.graph_steps <= 0) ctx->opt.graph_steps = 32;
+  if (ctx->opt.timeout_ns <= 0) ctx->opt.timeout_ns = 2000000000LL;
+  auto bail = [&](int rc) {
+    g_create_error = ctx->err;
+    vgtb_destroy(ctx);
+    return rc;
+  };
+  if (ctx->opt.precision != VGTB_FP64 && ctx->opt.precision != VGTB_SPLIT_BF16X3)
+    return bail(fail(ctx, VGTB_E_INVALID, "unknown precision %d", ctx->opt.precision));
+  if (ctx->opt.init != VGTB_INIT_GROUND && ctx->opt.init != VGTB_INIT_USER)
+    return bail(fail(ctx, VGTB_E_INVALID, "unknown init %d", ctx->opt.init));
+  ctx->split = ctx->opt.precision == VGTB_SPLIT_BF16X3;
+  ctx->delta = ctx->split || ctx->opt.delta_form != 0;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return bail(fail(ctx, VGTB_E_CUDA, "no CUDA device"));
+  if (ctx->split && !tc_gemm_supported())
+    return bail(fail(ctx, VGTB_E_UNSUPPORTED, "split precision needs an sm_103a (GB300) device"));
+  if (ctx->opt.cuda_stream) {
+    ctx->stream = (cudaStream_t)ctx->opt.cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess)
+      return bail(fail(ctx, VGTB_E_CUDA, "stream creation failed"));
+    ctx->own_stream = true;
+  }
+  if (cusolverDnCreate(&ctx->solver) != CUSOLVER_STATUS_SUCCESS)
+    return bail(fail(ctx, VGTB_E_CUDA, "cusolverDnCreate failed"));
+  cusolverDnSetStream(ctx->solver, ctx->stream);
+  for (int t = 0; t < n_traj; ++t)
+    if (traj_sys[t] < 0 || traj_sys[t] >= n_sys)
+      return bail(fail(ctx, VGTB_E_INVALID, "traj_sys[%d] = %d out of range", t, traj_sys[t]));
+  const double dt0 = sys[0].dt;
+  for (int s = 0; s < n_sys; ++s)
+    if (sys[s].dt != dt0) return bail(fail(ctx, VGTB_E_INVALID, "all systems of a batch share one dt"));
+  ctx->sys.resize(n_sys);
+  std::vector<DevSys> dsys(n_sys);
+  int rc;
+  for (int s = 0; s < n_sys; ++s) {
+    rc = prepare_system(ctx, s, sys[s], ctx->sys[s], dsys[s], ctx->opt.init == VGTB_INIT_GROUND);
+    if (rc) return bail(rc);
+    ctx->max_nat = std::max(ctx->max_nat, ctx->sys[s].nat);
+    ctx->max_Np = std::max(ctx->max_Np, ctx->sys[s].Np);
+  }
+  if (scc_configure(ctx->max_nat)) return bail(fail(ctx, VGTB_E_CUDA, "k_scc shared memory configuration failed"));
+  if ((rc = upload(ctx, &ctx->d_sys, dsys.data(), dsys.size()))) return bail(rc);
+  // trajectories and items; the split form keeps each operand family of a
+  // system contiguous over its items so that one 4-D tensor map covers it
+  ctx->trj.resize(n_traj);
+  std::vector<int> wpre(n_traj + 1, 0);
+  std::vector<int> sys_items(n_sys, 0), sys_next(n_sys, 0);
+  for (int t = 0; t < n_traj; ++t) sys_items[traj_sys[t]] += ctx->sys[traj_sys[t]].nk;
+  struct Fam {
+    __nv_bfloat16 *dD = nullptr, *Hemb = nullptr, *dHemb = nullptr, *Wemb = nullptr;
+    float* Xf = nullptr;
+  };
+  std::vector<Fam> fam(n_sys);
+  if (ctx->split) {
+    for (int s = 0; s < n_sys; ++s) {
+      const size_t NN = (size_t)ctx->sys[s].Np * ctx->sys[s].Np, ni = sys_items[s];
+      if (ni == 0) continue;
+      if ((rc = dalloc(ctx, &fam[s].dD, 4 * NN * ni))) return bail(rc);
+      if ((rc = dalloc(ctx, &fam[s].Hemb, 8 * NN * ni))) return bail(rc);
+      if ((rc = dalloc(ctx, &fam[s].dHemb, 8 * NN * ni))) return bail(rc);
+      if ((rc = dalloc(ctx, &fam[s].Wemb, 8 * NN * ni))) return bail(rc);
+      if ((rc = dalloc(ctx, &fam[s].Xf, 2 * NN * ni))) return bail(rc);
+    }
+  }
+  for (int t = 0; t < n_traj; ++t) {
+    HostTraj& T = ctx->trj[t];
+    HostSys& h = ctx->sys[traj_sys[t]];
+    T.sys = traj_sys[t];
+    T.item0 = (int)ctx->items_h.size();
+    h.trajs.push_back(t);
+    wpre[t + 1] = wpre[t] + h.n_tgt;
+    const size_t NN = (size_t)h.Np * h.Np;
+    for (int k = 0; k < h.nk; ++k) {
+      DevItem it;
+      memset(&it, 0, sizeof(it));
+      it.sys = T.sys;
+      it.traj = t;
+      it.k = k;
+      double2* lv = nullptr;
+      if ((rc = dalloc(ctx, &lv, 2 * NN))) return bail(rc);
+      it.D[0] = lv;
+      it.D[1] = lv + NN;
+      if (ctx->split) {
+        const size_t li = sys_next[T.sys]++;
+        it.dD_p = fam[T.sys].dD + 4 * NN * li;
+        it.Hemb_p = fam[T.sys].Hemb + 8 * NN * li;
+        it.dHemb_p = fam[T.sys].dHemb + 8 * NN * li;
+        it.Wemb_p = fam[T.sys].Wemb + 8 * NN * li;
+        it.Xf = fam[T.sys].Xf + 2 * NN * li;
+      } else {
+        if ((rc = dalloc(ctx, &it.H, NN))) return bail(rc);
+        if ((rc = dalloc(ctx, &it.W, NN))) return bail(rc);
+        if ((rc = dalloc(ctx, &it.X, NN))) return bail(rc);
+        if (ctx->delta && (rc = dalloc(ctx, &it.dH, NN))) return bail(rc);
+      }
+      ctx->items_h.push_back(it);
+    }
+    if ((rc = dalloc(ctx, &T.dq, h.nat))) return bail(rc);
+    if ((rc = dalloc(ctx, &T.eps, h.nat))) return bail(rc);
+    if ((rc = dalloc(ctx, &T.part, 5 * (size_t)h.n_tgt))) return bail(rc);
+    if ((rc = dalloc(ctx, &T.status, 1))) return bail(rc);
+  }
+  ctx->n_items = (int)ctx->items_h.size();
+  ctx->total_warps = wpre[n_traj];
+  if ((rc = upload(ctx, &ctx->d_wpre, wpre.data(), wpre.size()))) return bail(rc);
+  if ((rc = upload(ctx, &ctx->d_items, ctx->items_h.data(), ctx->items_h.size()))) return bail(rc);
+  if ((rc = dalloc(ctx, &ctx->d_trj, n_traj))) return bail(rc);
+  if ((rc = dalloc(ctx, &ctx->d_step, 1))) return bail(rc);
+  if ((rc = dalloc(ctx, &ctx->d_counter, 1))) return bail(rc);
+  if ((rc = upload_traj_table(ctx))) return bail(rc);
+  // work lists of the FP64 products and of the leapfrog
+  std::vector<GemmF64Item> g1(ctx->n_items), g2(ctx->n_items);
+  std::vector<LeapItem> lv(ctx->n_items);
+  for (int i = 0; i < ctx->n_items; ++i) {
+    const DevItem& it = ctx->items_h[i];
+    const HostSys& h = ctx->sys[it.sys];
+    const size_t NN = (size_t)h.Np * h.Np;
+    GemmF64Item a{}, b{};
+    a.A[0] = it.D[0];
+    a.a_par[0] = (long long)NN;
+    a.R[0] = it.H;
+    a.K[0] = h.Np;
+    a.lda[0] = a.ldr[0] = h.Np;
+    a.nseg = 1;
+    if (ctx->delta) {
+      a.A[1] = h.D0 + it.k * NN;
+      a.R[1] = it.dH;
+      a.K[1] = h.Np;
+      a.lda[1] = a.ldr[1] = h.Np;
+      a.nseg = 2;
+    }
+    a.M = a.N = a.ldc = h.Np;
+    a.C = it.W;
+    b.A[0] = h.Sinv + it.k * NN;
+    b.R[0] = it.W;
+    b.K[0] = h.Np;
+    b.lda[0] = b.ldr[0] = h.Np;
+    b.nseg = 1;
+    b.M = b.N = b.ldc = h.Np;
+    b.C = it.X;
+    g1[i] = a;
+    g2[i] = b;
+    LeapItem l{};
+    l.X = ctx->split ? (const void*)it.Xf : (const void*)it.X;
+    l.R0 = ctx->delta ? h.R0 + it.k * NN : nullptr;
+    l.D[0] = it.D[0];
+    l.D[1] = it.D[1];
+    l.pieces = it.dD_p;
+    l.Np = h.Np;
+    l.mode = 0;
+    lv[i] = l;
+  }
+  if (!ctx->split) {
+    if ((rc = upload(ctx, &ctx->d_g1, g1.data(), g1.size()))) return bail(rc);
+    if ((rc = upload(ctx, &ctx->d_g2, g2.data(), g2.size()))) return bail(rc);
+  }
+  if ((rc = upload(ctx, &ctx->d_leap, lv.data(), lv.size()))) return bail(rc);
+  // setup: S^-1, ground state
+  for (int s = 0; s < n_sys; ++s) {
+    if ((rc = build_sinv(ctx, s))) return bail(rc);
+  }
+  if (ctx->split) {
+    std::vector<TcSysView> views(n_sys);
+    for (int s = 0; s < n_sys; ++s) {
+      views[s].Np = ctx->sys[s].Np;
+      views[s].nk = ctx->sys[s].nk;
+      views[s].n_items = sys_items[s];
+      views[s].Sinv_p = ctx->sys[s].Sinv_p;
+      views[s].D0_p = ctx->sys[s].D0_p;
+      views[s].dD_p = fam[s].dD;
+      views[s].Hemb_p = fam[s].Hemb;
+      views[s].dHemb_p = fam[s].dHemb;
+      views[s].Wemb_p = fam[s].Wemb;
+    }
+    std::string msg;
+    if (tc_build_plans(views, ctx->items_h, ctx->opt.timeout_ns, ctx->opt.autotune, ctx->stream, &ctx->tc1, &ctx->tc2,
+                       &msg))
+      return bail(fail(ctx, VGTB_E_CUDA, "tcgen05 plan: %s", msg.c_str()));
+  }
+  if (ctx->opt.init == VGTB_INIT_GROUND) {
+    for (int s = 0; s < n_sys; ++s) {
+      if ((rc = ground_state(ctx, s))) return bail(rc);
+      if ((rc = finish_density(ctx, s))) return bail(rc);
+    }
+    if ((rc = reset_all(ctx))) return bail(rc);
+  }
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return bail(fail(ctx, VGTB_E_CUDA, "setup failed: %s", cudaGetErrorString(e)));
+  *out = ctx;
+  return VGTB_OK;
+}
+
+int vgtb_set_density(vgtb_ctx* ctx, int s, int k, const double* d0) {
+  if (!ctx) return VGTB_E_INVALID;
+  if (s < 0 || s >= (int)ctx->sys.size()) return fail(ctx, VGTB_E_INVALID, "system index %d out of range", s);
+  HostSys& h = ctx->sys[s];
+  if (k < 0 || k >= h.nk) return fail(ctx, VGTB_E_INVALID, "k index %d out of range", k);
+  if (!d0 || !finite_all(d0, 2 * (size_t)h.N * h.N)) return fail(ctx, VGTB_E_INVALID, "density is NULL or non-finite");
+  const size_t NN = (size_t)h.Np * h.Np;
+  CK(cudaMemcpy2DAsync(h.D0 + k * NN, sizeof(double2) * h.Np, d0, sizeof(double2) * h.N, sizeof(double2) * h.N, h.N,
+                       cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  // the system is ready once every k has been set
+  h.k_set.resize(h.nk, 0);
+  h.k_set[k] = 1;
+  bool all = true;
+  for (char c : h.k_set) all &= c != 0;
+  if (all || h.density_set) {
+    TRY(finish_density(ctx, s));
+    TRY(reset_all(ctx));
+  }
+  return VGTB_OK;
+}
+
+int vgtb_set_field(vgtb_ctx* ctx, int t, int n_times, const double* A) {
+  if (!ctx) return VGTB_E_INVALID;
+  if (t < 0 || t >= (int)ctx->trj.size()) return fail(ctx, VGTB_E_INVALID, "trajectory %d out of range", t);
+  if (n_times < 1 || !A || !finite_all(A, 3 * (size_t)n_times))
+    return fail(ctx, VGTB_E_INVALID, "field table is empty or non-finite");
+  HostTraj& T = ctx->trj[t];
+  const HostSys& h = ctx->sys[T.sys];
+  if (T.n_times != n_times) {
+    const int stride = ctx->opt.obs_stride;
+    TRY(dalloc(ctx, &T.A, 3 * (size_t)n_times));
+    TRY(dalloc(ctx, &T.J, 3 * (size_t)n_times));
+    TRY(dalloc(ctx, &T.E, (size_t)n_times));
+    TRY(dalloc(ctx, &T.q, (size_t)((n_times - 1) / stride + 1) * h.nat));
+    T.n_times = n_times;
+  }
+  CK(cudaMemcpyAsync(T.A, A, sizeof(double) * 3 * n_times, cudaMemcpyHostToDevice, ctx->stream));
+  TRY(upload_traj_table(ctx));
+  return reset_all(ctx);
+}
+
+int vgtb_propagate(vgtb_ctx* ctx, int nsteps) {
+  if (!ctx) return VGTB_E_INVALID;
+  if (nsteps < 0) return fail(ctx, VGTB_E_INVALID, "nsteps < 0");
+  for (auto& h : ctx->sys)
+    if (!h.density_set) return fail(ctx, VGTB_E_STATE, "no initial density set");
+  for (size_t t = 0; t < ctx->trj.size(); ++t)
+    if (ctx->trj[t].n_times < ctx->n_done + nsteps + 1)
+      return fail(ctx, VGTB_E_STATE, "trajectory %zu: field table has %d levels, step %d needs %d", t,
+                  ctx->trj[t].n_times, ctx->n_done + nsteps, ctx->n_done + nsteps + 1);
+  const int G = ctx->opt.graph_steps;
+  int left = nsteps;
+  if (G > 1 && left >= G) {
+    if (!ctx->graph || ctx->graph_steps != G || ctx->graph_profiled != ctx->profile) TRY(build_graph(ctx, G));
+    while (left >= G) {
+      CK(cudaGraphLaunch(ctx->graph, ctx->stream));
+      if (ctx->profile) TRY(accumulate_events(ctx, G));
+      left -= G;
+    }
+  }
+  while (left > 0) {
+    const int chunk = std::min(left, 64);
+    if (ctx->profile) TRY(ensure_events(ctx, chunk));
+    for (int s = 0; s < chunk; ++s) TRY(enqueue_step(ctx, ctx->profile ? &ctx->ev[7 * s] : nullptr));
+    if (ctx->profile) TRY(accumulate_events(ctx, chunk));
+    left -= chunk;
+  }
+  // observables of the final level
+  const int nt = (int)ctx->trj.size();
+  launch_obs(ctx->d_sys, ctx->d_trj, ctx->d_items, ctx->d_wpre, nt, ctx->total_warps, ctx->d_step, ctx->delta ? 1 : 0,
+             -1, ctx->stream);
+  launch_scc(ctx->d_sys, ctx->d_trj, nt, ctx->d_step, ctx->opt.obs_stride, -1, 1, ctx->max_nat, ctx->stream);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->n_done += nsteps;
+  return check_status(ctx);
+}
+
+int vgtb_steps_done(const vgtb_ctx* ctx) { return ctx ? ctx->n_done : -1; }
+
+int vgtb_observables(vgtb_ctx* ctx, int t, double* J, double* E, double* q) {
+  if (!ctx) return VGTB_E_INVALID;
+  if (t < 0 || t >= (int)ctx->trj.size()) return fail(ctx, VGTB_E_INVALID, "trajectory %d out of range", t);
+  const HostTraj& T = ctx->trj[t];
+  if (!T.J) return fail(ctx, VGTB_E_STATE, "no field set for trajectory %d", t);
+  const int n = ctx->n_done + 1;
+  if (J) CK(cudaMemcpyAsync(J, T.J, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, ctx->stream));
+  if (E) CK(cudaMemcpyAsync(E, T.E, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream));
+  if (q) {
+    const int nq = ctx->n_done / ctx->opt.obs_stride + 1;
+    CK(cudaMemcpyAsync(q, T.q, sizeof(double) * nq * ctx->sys[T.sys].nat, cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  return VGTB_OK;
+}
+
+int vgtb_get_density(vgtb_ctx* ctx, int t, int k, double* d_out) {
+  if (!ctx) return VGTB_E_INVALID;
+  if (t < 0 || t >= (int)ctx->trj.size()) return fail(ctx, VGTB_E_INVALID, "trajectory %d out of range", t);
+  const HostTraj& T = ctx->trj[t];
+  const HostSys& h = ctx->sys[T.sys];
+  if (k < 0 || k >= h.nk || !d_out) return fail(ctx, VGTB_E_INVALID, "bad k or NULL output");
+  const DevItem& it = ctx->items_h[T.item0 + k];
+  const size_t NN = (size_t)h.Np * h.Np;
+  const int cur = ctx->n_done & 1;
+  std::vector<double2> a(NN), b;
+  CK(cudaMemcpyAsync(a.data(), it.D[cur], NN * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream));
+  if (ctx->delta) {
+    b.resize(NN);
+    CK(cudaMemcpyAsync(b.data(), h.D0 + it.k * NN, NN * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (int i = 0; i < h.N; ++i)
+    for (int j = 0; j < h.N; ++j) {
+      double2 v = a[(size_t)i * h.Np + j];
+      if (ctx->delta) {
+        v.x += b[(size_t)i * h.Np + j].x;
+        v.y += b[(size_t)i * h.Np + j].y;
+      }
+      d_out[2 * ((size_t)i * h.N + j)] = v.x;
+      d_out[2 * ((size_t)i * h.N + j) + 1] = v.y;
+    }
+  return VGTB_OK;
+}
+
+int vgtb_get_initial_density(vgtb_ctx* ctx, int s, int k, double* d_out) {
+  if (!ctx) return VGTB_E_INVALID;
+  if (s < 0 || s >= (int)ctx->sys.size()) return fail(ctx, VGTB_E_INVALID, "system index %d out of range", s);
+  const HostSys& h = ctx->sys[s];
+  if (k < 0 || k >= h.nk || !d_out) return fail(ctx, VGTB_E_INVALID, "bad k or NULL output");
+  if (!h.density_set) return fail(ctx, VGTB_E_STATE, "no initial density set");
+  const size_t NN = (size_t)h.Np * h.Np;
+  CK(cudaMemcpy2DAsync(d_out, sizeof(double2) * h.N, h.D0 + k * NN, sizeof(double2) * h.Np, sizeof(double2) * h.N,
+                       h.N, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return VGTB_OK;
+}
+
+long long vgtb_state_size(const vgtb_ctx* ctx) {
+  if (!ctx) return -1;
+  long long b = 4 * sizeof(long long);
+  for (auto& it : ctx->items_h) {
+    const HostSys& h = ctx->sys[it.sys];
+    b += 2LL * h.Np * h.Np * (long long)sizeof(double2);
+  }
+  return b;
+}
+
+int vgtb_get_state(vgtb_ctx* ctx, void* buf, long long bytes) {
+  if (!ctx || !buf) return VGTB_E_INVALID;
+  if (bytes < vgtb_state_size(ctx)) return fail(ctx, VGTB_E_INVALID, "state buffer too small");
+  long long* hd = (long long*)buf;
+  hd[0] = 0x7674627374617465LL;  // tag
+  hd[1] = ctx->n_done;
+  hd[2] = ctx->n_items;
+  hd[3] = ctx->delta ? 1 : 0;
+  char* p = (char*)buf + 4 * sizeof(long long);
+  for (auto& it : ctx->items_h) {
+    const HostSys& h = ctx->sys[it.sys];
+    const size_t NN = (size_t)h.Np * h.Np;
+    CK(cudaMemcpyAsync(p, it.D[0], 2 * NN * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream));
+    p += 2 * NN * sizeof(double2);
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  return VGTB_OK;
+}
+
+int vgtb_set_state(vgtb_ctx* ctx, const void* buf, long long bytes) {
+  if (!ctx || !buf) return VGTB_E_INVALID;
+  if (bytes < vgtb_state_size(ctx)) return fail(ctx, VGTB_E_INVALID, "state buffer too small");
+  const long long* hd = (const long long*)buf;
+  if (hd[0] != 0x7674627374617465LL || hd[2] != ctx->n_items || hd[3] != (ctx->delta ? 1 : 0))
+    return fail(ctx, VGTB_E_INVALID, "state does not belong to a context of this shape");
+  const int n = (int)hd[1];
+  for (auto& t : ctx->trj)
+    if (t.n_times < n + 1) return fail(ctx, VGTB_E_STATE, "field table shorter than the saved step");
+  const char* p = (const char*)buf + 4 * sizeof(long long);
+  for (auto& it : ctx->items_h) {
+    const HostSys& h = ctx->sys[it.sys];
+    const size_t NN = (size_t)h.Np * h.Np;
+    CK(cudaMemcpyAsync(it.D[0], p, 2 * NN * sizeof(double2), cudaMemcpyHostToDevice, ctx->stream));
+    if (it.dD_p) launch_split_planar(it.D[n & 1], it.dD_p, h.N, h.Np, ctx->stream);
+    p += 2 * NN * sizeof(double2);
+  }
+  CK(cudaMemcpyAsync(ctx->d_step, &n, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemsetAsync(ctx->d_counter, 0, sizeof(int), ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->n_done = n;
+  return VGTB_OK;
+}
+
+int vgtb_profile(vgtb_ctx* ctx, int enable) {
+  if (!ctx) return VGTB_E_INVALID;
+  ctx->profile = enable != 0;
+  for (int c = 0; c < VGTB_K_COUNT; ++c) {
+    ctx->prof_ms[c] = 0.0;
+    ctx->prof_launch[c] = 0;
+  }
+  return VGTB_OK;
+}
+
+int vgtb_kernel_stats(vgtb_ctx* ctx, long long* launches, double* ms, int n) {
+  if (!ctx) return VGTB_E_INVALID;
+  for (int c = 0; c < std::min(n, (int)VGTB_K_COUNT); ++c) {
+    if (launches) launches[c] = ctx->prof_launch[c];
+    if (ms) ms[c] = ctx->prof_ms[c];
+  }
+  return VGTB_K_COUNT;
+}
+
+const char* vgtb_last_error(const vgtb_ctx* ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
+
+void vgtb_destroy(vgtb_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  drop_graph(ctx);
+  for (auto e : ctx->ev) cudaEventDestroy(e);
+  tc_destroy_plan(ctx->tc1);
+  tc_destroy_plan(ctx->tc2);
+  for (void* p : ctx->allocs) cudaFree(p);
+  if (ctx->solver) cusolverDnDestroy(ctx->solver);
+  if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+}  // extern "C"

@@ -1,0 +1,105 @@
+// vgtb_diag_split_chain: the two tcgen05 products on caller matrices (unit test hook).
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/vgtb.h"
+#include "../../include/vgtb_diag.h"
+#include "vgtb_internal.h"
+#include "vgtb_tc.h"
+
+using namespace vgtb;
+
+namespace {
+struct Scratch {
+  std::vector<void*> p;
+  ~Scratch() {
+    for (void* q : p) cudaFree(q);
+  }
+  template <class T>
+  T* get(size_t n) {
+    void* q = nullptr;
+    if (cudaMalloc(&q, n * sizeof(T)) != cudaSuccess) return nullptr;
+    cudaMemset(q, 0, n * sizeof(T));
+    p.push_back(q);
+    return (T*)q;
+  }
+};
+
+void to_padded(const double* src, std::vector<double2>& dst, int n, int Np) {
+  dst.assign((size_t)Np * Np, make_double2(0.0, 0.0));
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) dst[(size_t)i * Np + j] = make_double2(src[2 * ((size_t)i * n + j)], src[2 * ((size_t)i * n + j) + 1]);
+}
+}  // namespace
+
+extern "C" int vgtb_diag_split_chain(int n, const double* a, const double* r, const double* s, double* w_out,
+                                     double* x_out) {
+  if (n < 1 || !a || !r || !s || !w_out || !x_out) return VGTB_E_INVALID;
+  if (!tc_gemm_supported()) return VGTB_E_UNSUPPORTED;
+  const int Np = (n + 127) / 128 * 128;
+  const size_t NN = (size_t)Np * Np;
+  Scratch m;
+  double2* dsrc = m.get<double2>(NN);
+  __nv_bfloat16* a_p = m.get<__nv_bfloat16>(4 * NN);
+  __nv_bfloat16* d0_p = m.get<__nv_bfloat16>(4 * NN);
+  __nv_bfloat16* s_p = m.get<__nv_bfloat16>(4 * NN);
+  __nv_bfloat16* r_e = m.get<__nv_bfloat16>(8 * NN);
+  __nv_bfloat16* z_e = m.get<__nv_bfloat16>(8 * NN);
+  __nv_bfloat16* w_e = m.get<__nv_bfloat16>(8 * NN);
+  float* xf = m.get<float>(2 * NN);
+  if (!dsrc || !a_p || !d0_p || !s_p || !r_e || !z_e || !w_e || !xf) return VGTB_E_NOMEM;
+  cudaStream_t st = 0;
+  std::vector<double2> h;
+  to_padded(a, h, n, Np);
+  cudaMemcpy(dsrc, h.data(), NN * sizeof(double2), cudaMemcpyHostToDevice);
+  launch_split_planar(dsrc, a_p, n, Np, st);
+  cudaDeviceSynchronize();
+  to_padded(s, h, n, Np);
+  cudaMemcpy(dsrc, h.data(), NN * sizeof(double2), cudaMemcpyHostToDevice);
+  launch_split_planar(dsrc, s_p, n, Np, st);
+  cudaDeviceSynchronize();
+  to_padded(r, h, n, Np);
+  cudaMemcpy(dsrc, h.data(), NN * sizeof(double2), cudaMemcpyHostToDevice);
+  launch_split_embedded(dsrc, r_e, Np, st);
+  if (cudaDeviceSynchronize() != cudaSuccess) return VGTB_E_CUDA;
+  std::vector<TcSysView> views(1);
+  views[0].Np = Np;
+  views[0].nk = 1;
+  views[0].n_items = 1;
+  views[0].Sinv_p = s_p;
+  views[0].D0_p = d0_p;
+  views[0].dD_p = a_p;
+  views[0].Hemb_p = r_e;
+  views[0].dHemb_p = z_e;
+  views[0].Wemb_p = w_e;
+  std::vector<DevItem> items(1);
+  memset(&items[0], 0, sizeof(DevItem));
+  items[0].Wemb_p = w_e;
+  items[0].Xf = xf;
+  TcPlan *p1 = nullptr, *p2 = nullptr;
+  std::string msg;
+  if (tc_build_plans(views, items, 2000000000LL, 0, st, &p1, &p2, &msg)) return VGTB_E_CUDA;
+  int rc = VGTB_OK;
+  if (tc_launch(p1, st) || tc_launch(p2, st)) rc = VGTB_E_CUDA;
+  if (cudaDeviceSynchronize() != cudaSuccess) rc = VGTB_E_CUDA;
+  if (rc == VGTB_OK && (tc_status(p1, st) || tc_status(p2, st))) rc = VGTB_E_TIMEOUT;
+  tc_destroy_plan(p1);
+  tc_destroy_plan(p2);
+  if (rc != VGTB_OK) return rc;
+  std::vector<__nv_bfloat16> we(8 * NN);
+  std::vector<float> xh(2 * NN);
+  cudaMemcpy(we.data(), w_e, 8 * NN * sizeof(__nv_bfloat16), cudaMemcpyDeviceToHost);
+  cudaMemcpy(xh.data(), xf, 2 * NN * sizeof(float), cudaMemcpyDeviceToHost);
+  const size_t ld = 2 * (size_t)Np, P = 4 * NN;
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      const size_t o = 2 * ((size_t)i * n + j);
+      w_out[o] = (double)__bfloat162float(we[i * ld + j]) + (double)__bfloat162float(we[P + i * ld + j]);
+      w_out[o + 1] = (double)__bfloat162float(we[i * ld + Np + j]) + (double)__bfloat162float(we[P + i * ld + Np + j]);
+      x_out[o] = xh[i * ld + j];
+      x_out[o + 1] = xh[i * ld + Np + j];
+    }
+  return VGTB_OK;
+}

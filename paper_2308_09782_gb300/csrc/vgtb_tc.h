@@ -1,0 +1,35 @@
+// Host interface of the tcgen05 split-precision complex products (k_gemm_tc.cu).
+#pragma once
+#include <string>
+#include <vector>
+
+#include "vgtb_internal.h"
+
+namespace vgtb {
+
+struct TcPlan;  // tensor maps, problem table and launch shape of one product
+
+// Operand families of one system, each contiguous over that system's items
+// (items in creation order: trajectory-major, k-minor).
+struct TcSysView {
+  int Np, nk, n_items;
+  __nv_bfloat16* Sinv_p;   // [nk][2][Np][2Np]
+  __nv_bfloat16* D0_p;     // [nk][2][Np][2Np]
+  __nv_bfloat16* dD_p;     // [n_items][2][Np][2Np]
+  __nv_bfloat16* Hemb_p;   // [n_items][2][2Np][2Np]
+  __nv_bfloat16* dHemb_p;  // [n_items][2][2Np][2Np]
+  __nv_bfloat16* Wemb_p;   // [n_items][2][2Np][2Np]
+};
+
+// Plans for the two products of the split form, over every item:
+//   product 1: W = [dD | D0] [H | dH]^dagger  -> embedded BF16 hi/lo pieces of W
+//   product 2: X = S^-1 W^dagger               -> FP32 planar X
+// Returns 0 on success, else fills *msg.
+int tc_build_plans(const std::vector<TcSysView>& sys, const std::vector<DevItem>& items, long long timeout_ns,
+                   int autotune, cudaStream_t st, TcPlan** p1, TcPlan** p2, std::string* msg);
+int tc_launch(TcPlan* p, cudaStream_t st);
+int tc_status(TcPlan* p, cudaStream_t st);  // 0 or the plan's device error word
+void tc_destroy_plan(TcPlan* p);
+int tc_plan_variant(const TcPlan* p);  // index of the tile variant the plan uses
+
+}  // namespace vgtb

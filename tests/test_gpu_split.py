@@ -1,0 +1,75 @@
+"""The tcgen05 split-precision form against numpy and against the FP64 oracle.
+
+Product-level tolerance: BF16 hi/lo pieces carry ~2^-17 relative precision and
+three partial products are accumulated in FP32, so a relative Frobenius error
+of 3e-5 bounds one product.  Propagation tolerance (BASELINE target): J(t)
+within 1e-4 relative of the FP64 oracle.
+"""
+import numpy as np
+import pytest
+
+from tests._gpu_util import gpu_run, oracle_ground, oracle_run, rel_fro, system
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2308_09782_gb300 import vgtb
+    vgtb.load()
+
+
+@pytest.mark.parametrize("n", [128, 200, 384, 1000])
+def test_split_products_match_numpy(n):
+    from paper_2308_09782_gb300 import vgtb
+    rng = np.random.default_rng(n)
+    def rnd():
+        return rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n))
+    a, r, s = rnd(), rnd(), rnd()
+    w, x = vgtb.diag_split_chain(a, r, s)
+    w_ref = a @ r.conj().T
+    assert rel_fro([w], [w_ref]) < 3e-5
+    x_ref = s @ w_ref.conj().T
+    assert rel_fro([x], [x_ref]) < 6e-5
+    # structure: a transposed operand or a lost sign would give O(1) errors
+    assert rel_fro([x], [s @ w_ref]) > 0.1
+
+
+@pytest.mark.parametrize("name,nsteps", [("si8_pulse", 1000), ("si64_pulse", 2000)])
+def test_split_propagation_matches_oracle(name, nsteps):
+    from paper_2308_09782_gb300 import vgtb
+    ref = oracle_run(name, nsteps)
+    with gpu_run(name, nsteps, precision=vgtb.SPLIT_BF16X3) as c:
+        J, E, q = c.observables(0)
+        D = [c.get_density(0, k) for k in range(8)]
+    err_j = rel_fro([J], [ref["J"]])
+    err_d = rel_fro(D, ref["D"])
+    err_q = np.abs(q - ref["q"]).max()
+    err_e = np.abs(E - ref["E"]).max()
+    print(f"{name}: J {err_j:.3e}  D {err_d:.3e}  q {err_q:.3e}  E {err_e:.3e}")
+    assert err_j <= 1e-4
+    assert err_d <= 1e-4
+    assert err_q <= 1e-4
+
+
+def test_split_timeout_returns_error_and_context_recovers():
+    """A 1 ns wait limit makes the product kernels give up: E_TIMEOUT, no hang;
+    a fresh context afterwards works."""
+    from paper_2308_09782_gb300 import vgtb
+    name = "si8_pulse"
+    sysd, A, _ = system(name)
+    _, gs = oracle_ground(name)
+    c = vgtb.Context(sysd, precision=vgtb.SPLIT_BF16X3, init=vgtb.INIT_USER, timeout_ns=1)
+    for k, D in enumerate(gs["D"]):
+        c.set_density(0, k, D)
+    c.set_field(0, A[:6])
+    with pytest.raises(vgtb.VgtbError) as e:
+        c.propagate(5)
+    assert e.value.code == -8
+    c.close()
+    with gpu_run(name, 20, precision=vgtb.SPLIT_BF16X3) as ok:
+        J, _, _ = ok.observables(0)
+    assert np.all(np.isfinite(J))
