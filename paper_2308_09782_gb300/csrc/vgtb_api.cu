@@ -679,34 +679,41 @@ void drop_graph(vgtb_ctx* ctx) {
 }
 
 // ---------------------------------------------------------------------------
-// one step for every trajectory; ev != nullptr records 7 timing events
+// one step for every trajectory; ev != nullptr records 7 timing events (as
+// external event nodes when the stream is being captured into a graph)
 // ---------------------------------------------------------------------------
 int enqueue_step(vgtb_ctx* ctx, cudaEvent_t* ev) {
   cudaStream_t st = ctx->stream;
+  unsigned evflag = cudaEventRecordDefault;
+  if (ev) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(st, &cs));
+    if (cs == cudaStreamCaptureStatusActive) evflag = cudaEventRecordExternal;
+  }
   const int nt = (int)ctx->trj.size();
   const int stride = ctx->opt.obs_stride > 0 ? ctx->opt.obs_stride : 1;
-  if (ev) CK(cudaEventRecord(ev[0], st));
+  if (ev) CK(cudaEventRecordWithFlags(ev[0], st, evflag));
   launch_obs(ctx->d_sys, ctx->d_trj, ctx->d_items, ctx->d_wpre, nt, ctx->total_warps, ctx->d_step, ctx->delta ? 1 : 0,
              -1, st);
-  if (ev) CK(cudaEventRecord(ev[1], st));
+  if (ev) CK(cudaEventRecordWithFlags(ev[1], st, evflag));
   launch_scc(ctx->d_sys, ctx->d_trj, nt, ctx->d_step, stride, -1, 1, ctx->max_nat, st);
-  if (ev) CK(cudaEventRecord(ev[2], st));
+  if (ev) CK(cudaEventRecordWithFlags(ev[2], st, evflag));
   const int mode = ctx->split ? PH_SPLIT : (ctx->delta ? PH_FP64_DELTA : PH_FP64_PLAIN);
   launch_phase(ctx->d_sys, ctx->d_trj, ctx->d_items, ctx->d_wpre, nt, ctx->total_warps, ctx->d_step, mode, -1, st);
-  if (ev) CK(cudaEventRecord(ev[3], st));
+  if (ev) CK(cudaEventRecordWithFlags(ev[3], st, evflag));
   if (ctx->split) {
     TRY(tc_launch(ctx->tc1, st) == 0 ? VGTB_OK : fail(ctx, VGTB_E_CUDA, "tcgen05 product 1 launch failed"));
-    if (ev) CK(cudaEventRecord(ev[4], st));
+    if (ev) CK(cudaEventRecordWithFlags(ev[4], st, evflag));
     TRY(tc_launch(ctx->tc2, st) == 0 ? VGTB_OK : fail(ctx, VGTB_E_CUDA, "tcgen05 product 2 launch failed"));
   } else {
     launch_gemm_f64(ctx->d_g1, ctx->n_items, ctx->max_Np, ctx->max_Np, ctx->d_step, st);
-    if (ev) CK(cudaEventRecord(ev[4], st));
+    if (ev) CK(cudaEventRecordWithFlags(ev[4], st, evflag));
     launch_gemm_f64(ctx->d_g2, ctx->n_items, ctx->max_Np, ctx->max_Np, ctx->d_step, st);
   }
-  if (ev) CK(cudaEventRecord(ev[5], st));
+  if (ev) CK(cudaEventRecordWithFlags(ev[5], st, evflag));
   launch_leap(ctx->d_leap, ctx->n_items, ctx->max_Np, ctx->split ? 1 : 0, ctx->d_step, ctx->sys[0].dt,
               ctx->d_counter, ctx->d_step, st);
-  if (ev) CK(cudaEventRecord(ev[6], st));
+  if (ev) CK(cudaEventRecordWithFlags(ev[6], st, evflag));
   CK(cudaGetLastError());
   return VGTB_OK;
 }

@@ -99,11 +99,11 @@ def test_rerun_and_graph_are_bitwise_identical():
         assert np.array_equal(a.get_density(0, 3), g.get_density(0, 3))
 
 
-def _ctx_full_field(name):
+def _ctx_full_field(name, **opts):
     from paper_2308_09782_gb300 import vgtb
     sysd, A, n = system(name)
     _, gs = oracle_ground(name)
-    c = vgtb.Context(sysd, init=vgtb.INIT_USER)
+    c = vgtb.Context(sysd, init=vgtb.INIT_USER, **opts)
     for k, D in enumerate(gs["D"]):
         c.set_density(0, k, D)
     c.set_field(0, A)
@@ -181,3 +181,15 @@ def test_error_codes():
     with pytest.raises(vgtb.VgtbError) as e:
         vgtb.Context(s4)
     assert e.value.code == -1
+
+
+@pytest.mark.parametrize("graph_steps", [1, 16])
+def test_profiling_counts_every_kernel(graph_steps):
+    """vgtb_profile: events around every hot kernel, with and without graphs."""
+    with _ctx_full_field("si8_pulse", graph_steps=graph_steps) as c:
+        c.propagate(5)
+        c.profile(True)            # enable and reset the counters
+        c.propagate(40)
+        st = c.kernel_stats()
+    for k, (n, ms) in st.items():
+        assert n == 40 and ms > 0.0, (k, n, ms)
