@@ -175,6 +175,31 @@ const char* vgtb_last_error(const vgtb_ctx* ctx);
 /* Release the context and all its device memory.  NULL-safe. */
 void vgtb_destroy(vgtb_ctx* ctx);
 
+/* Complex product C = A R^dagger with the split-precision tcgen05 kernel of
+ * the propagation (BF16 hi/lo pieces, three products, FP32 accumulation), for
+ * callers that must not allocate device memory: code whose device memory is
+ * owned by another allocator (a framework caching allocator or a pool that has
+ * reserved the HBM, where a cudaMalloc fails or fragments it) and loops that
+ * cannot take the implicit device synchronisation of cudaMalloc/cudaFree.
+ * The paper has no counterpart; it is a library-level variant.
+ *
+ * a, r, c: DEVICE pointers to n x n complex matrices, row-major, interleaved
+ * (re, im) doubles, owned by the caller; c is written.  1 <= n <= 256.
+ * stream: cudaStream_t to run on (NULL = the legacy default stream); the call
+ * synchronises that stream before it returns.
+ * The call allocates nothing: its scratch (BF16 pieces, the FP32 product, a
+ * problem table and an error word, 2 MiB + 512 B) is one static device array
+ * that every GPU which loads the library holds until the process exits.  The
+ * first call on a device looks up the array's device address and raises the
+ * kernel's shared-memory limit; make that first call before any stream
+ * capture.  All calls share the array and it keeps the last call's contents
+ * (each call rewrites, zero padding included, everything it reads), so calls
+ * whose work overlaps on the GPU (other streams or host threads) race.
+ * Returns VGTB_OK; VGTB_E_INVALID for n outside 1..256 or a NULL pointer;
+ * VGTB_E_UNSUPPORTED without an sm_103a device; VGTB_E_TIMEOUT when a bounded
+ * device wait expired; VGTB_E_CUDA for a failed CUDA call. */
+int vgtb_split_cgemm_noalloc(int n, const double* a, const double* r, double* c, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

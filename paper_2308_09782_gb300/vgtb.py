@@ -29,7 +29,7 @@ EXPORTS = ["vgtb_default_options", "vgtb_create", "vgtb_create_batch", "vgtb_set
            "vgtb_set_field", "vgtb_propagate", "vgtb_steps_done", "vgtb_observables",
            "vgtb_get_density", "vgtb_get_initial_density", "vgtb_state_size", "vgtb_get_state", "vgtb_set_state",
            "vgtb_profile", "vgtb_kernel_stats", "vgtb_last_error", "vgtb_destroy",
-           "vgtb_diag_split_chain"]
+           "vgtb_diag_split_chain", "vgtb_split_cgemm_noalloc"]
 
 
 class VgtbSystem(C.Structure):
@@ -85,6 +85,7 @@ def load(path: str = LIB_PATH):
     lib.vgtb_destroy.argtypes = [ctxp]
     lib.vgtb_destroy.restype = None
     lib.vgtb_diag_split_chain.argtypes = [I, P(D), P(D), P(D), P(D), P(D)]
+    lib.vgtb_split_cgemm_noalloc.argtypes = [I, V, V, V, V]
     for name in EXPORTS:
         if name not in ("vgtb_default_options", "vgtb_last_error", "vgtb_destroy", "vgtb_state_size"):
             getattr(lib, name).restype = I
