@@ -1,12 +1,15 @@
 // Block-sparse kernels of one propagation step:
-//   k_obs   - Mulliken, current and energy partial sums from D_k(t_n) (Eqs. 10, 14)
-//   k_scc   - per-trajectory reduction: dq, eps = gamma dq, J, E (Eq. 10, Eq. 14)
-//   k_phase - Bloch sum of H_k(t_n) with the vector potential (Eqs. 7-12)
-// One warp handles one target (I, J) of one trajectory: it walks the target's
-// real-space images (blocks with different L), lanes over the n_I x n_J
-// elements, so the block values are read once, coalesced, per step.
-// All reductions use fixed orders (lane butterflies, strided loops, fixed
-// trees), so reruns are bitwise identical.
+//   k_obs         - Mulliken, current and energy partial sums from D_k(t_n) (Eqs. 10, 14)
+//   k_scc         - dq, eps = gamma dq, J, E per trajectory (Eq. 10, Eq. 14)
+//   k_phase       - Bloch sum of H_k(t_n) with the vector potential (Eqs. 7-12), FP64
+//   k_phase_split - the same sum in FP32, written as embedded BF16 hi/lo pieces
+// A half-warp (16 lanes) handles one target (I, J) of one trajectory: it walks the
+// target's real-space images (blocks with different L), lanes over the n_I x n_J
+// elements (16 for an sp3 pair; larger blocks loop), so the block values are read
+// once, coalesced, per step.  All reductions use fixed orders (lane butterflies,
+// strided loops, fixed trees, a last-CTA sum), so reruns are bitwise identical.
+// GB300 executes FP64 at a small fraction of its FP32 rate, so FP64 is kept to the
+// reductions that need it; the split form builds its BF16 operands in FP32.
 #include "vgtb_internal.h"
 
 namespace vgtb {
@@ -26,6 +29,28 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// sum over the 16 lanes of a half-warp (both halves reduce independently)
+__device__ __forceinline__ double half_sum(double v) {
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+struct Unit {
+  bool active;
+  int t, tg;
+};
+
+// unit = (trajectory, target), one per half-warp
+__device__ __forceinline__ Unit unit_of(const int* wpre, int n_traj, int total) {
+  const int u = (blockIdx.x * blockDim.x + threadIdx.x) >> 4;
+  Unit r;
+  r.active = u < total;
+  r.t = r.active ? find_traj(wpre, n_traj, u) : 0;
+  r.tg = r.active ? u - wpre[r.t] : 0;
+  return r;
+}
+
 // ---------------------------------------------------------------------------
 // Partial sums per target, summed over k with weights w_k:
 //   q   : sum Re(D_{mu nu} conj(S_k,mu nu))                 (Eq. 10: [D S]_{mu mu})
@@ -35,74 +60,76 @@ __device__ __forceinline__ double warp_sum(double v) {
 //   q += s Re u,  T_a += ds_a Im u + (A_a/c) s Re u,
 //   E += (h0 + alpha s) Re u + ((A/c).ds) Im u,   because P = i dS/dR_J.
 // ---------------------------------------------------------------------------
-__global__ void k_obs(const DevSys* __restrict__ sysv, const DevTraj* __restrict__ trj,
-                      const DevItem* __restrict__ items, const int* __restrict__ wpre, int n_traj,
-                      int total, const int* __restrict__ step, int delta, int fixed_step) {
-  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (w >= total) return;
-  const int t = find_traj(wpre, n_traj, w);
-  const int tg = w - wpre[t];
-  const DevTraj& T = trj[t];
-  const DevSys& S = sysv[T.sys];
-  const int n = fixed_step >= 0 ? fixed_step : *step;
-  const int par = n & 1;
-  double A0 = 0.0, A1 = 0.0, A2 = 0.0;
-  if (T.A) {
-    A0 = T.A[3 * n];
-    A1 = T.A[3 * n + 1];
-    A2 = T.A[3 * n + 2];
-  }
-  const double ic = 1.0 / kLight;
-  const double alpha = (A0 * A0 + A1 * A1 + A2 * A2) * 0.5 * ic * ic;
-  const int I = S.tgt_I[tg], J = S.tgt_J[tg];
-  const int oi = S.orb_off[I], ni = S.orb_off[I + 1] - oi;
-  const int oj = S.orb_off[J], nj = S.orb_off[J + 1] - oj;
-  const int nel = ni * nj;
-  const int g0 = S.tgt_img0[tg], g1 = S.tgt_img0[tg + 1];
-  const long long NN = (long long)S.Np * S.Np;
+__global__ void __launch_bounds__(256) k_obs(const DevSys* __restrict__ sysv, const DevTraj* __restrict__ trj,
+                                             const DevItem* __restrict__ items, const int* __restrict__ wpre,
+                                             int n_traj, int total, const int* __restrict__ step, int delta,
+                                             int fixed_step) {
+  const Unit U = unit_of(wpre, n_traj, total);
+  const int lane = threadIdx.x & 15;
   double aq = 0.0, ax = 0.0, ay = 0.0, az = 0.0, ae = 0.0;
-  for (int e = lane; e < nel; e += 32) {
-    const int a = e / nj, b = e - a * nj;
-    const long long idx = (long long)(oi + a) * S.Np + (oj + b);
+  const DevTraj& T = trj[U.t];
+  const DevSys& S = sysv[T.sys];
+  if (U.active) {
+    const int n = fixed_step >= 0 ? fixed_step : *step;
+    const int par = n & 1;
+    double A0 = 0.0, A1 = 0.0, A2 = 0.0;
+    if (T.A) {
+      A0 = T.A[3 * n];
+      A1 = T.A[3 * n + 1];
+      A2 = T.A[3 * n + 2];
+    }
+    const double ic = 1.0 / kLight;
+    const double alpha = (A0 * A0 + A1 * A1 + A2 * A2) * 0.5 * ic * ic;
+    const double a0 = A0 * ic, a1 = A1 * ic, a2 = A2 * ic;
+    const int I = S.tgt_I[U.tg], J = S.tgt_J[U.tg];
+    const int oi = S.orb_off[I], ni = S.orb_off[I + 1] - oi;
+    const int oj = S.orb_off[J], nj = S.orb_off[J + 1] - oj;
+    const int nel = ni * nj;
+    const int g0 = S.tgt_img0[U.tg], g1 = S.tgt_img0[U.tg + 1];
+    const long long NN = (long long)S.Np * S.Np;
     for (int k = 0; k < S.nk; ++k) {
-      const DevItem& it = items[T.item0 + k];
-      double2 d = it.D[par][idx];
-      if (delta) {
-        const double2 d0 = S.D0[k * NN + idx];
-        d.x += d0.x;
-        d.y += d0.y;
-      }
+      const double2* Dk = items[T.item0 + k].D[par];
+      const double2* D0k = S.D0 + k * NN;
       const double wk = S.wk[k];
-      double lq = 0.0, lx = 0.0, ly = 0.0, lz = 0.0, le = 0.0;
-      for (int g = g0; g < g1; ++g) {
-        const int blk = S.img_blk[g];
-        const long long off = S.blk_off[blk] + e;
-        const double sv = S.s[off], hv = S.h0[off];
-        const double dx = S.ds[off], dy = S.ds[S.ds_stride + off], dz = S.ds[2 * S.ds_stride + off];
-        const double2 ph = S.phase[(long long)k * S.n_blk + blk];
-        const double ur = d.x * ph.x + d.y * ph.y;
-        const double ui = d.y * ph.x - d.x * ph.y;
-        lq += sv * ur;
-        lx += dx * ui + A0 * ic * sv * ur;
-        ly += dy * ui + A1 * ic * sv * ur;
-        lz += dz * ui + A2 * ic * sv * ur;
-        le += (hv + alpha * sv) * ur + (A0 * dx + A1 * dy + A2 * dz) * ic * ui;
+      for (int e = lane; e < nel; e += 16) {
+        const int a = e / nj, b = e - a * nj;
+        const long long idx = (long long)(oi + a) * S.Np + (oj + b);
+        double2 d = Dk[idx];
+        if (delta) {
+          const double2 d0 = D0k[idx];
+          d.x += d0.x;
+          d.y += d0.y;
+        }
+        double lq = 0.0, lx = 0.0, ly = 0.0, lz = 0.0, le = 0.0;
+        for (int g = g0; g < g1; ++g) {
+          const long long off = S.img_off[g] + e;
+          const double sv = S.s[off], hv = S.h0[off];
+          const double dx = S.ds[off], dy = S.ds[S.ds_stride + off], dz = S.ds[2 * S.ds_stride + off];
+          const double2 ph = S.phase[(long long)k * S.n_blk + S.img_blk[g]];
+          const double ur = d.x * ph.x + d.y * ph.y;
+          const double ui = d.y * ph.x - d.x * ph.y;
+          const double sur = sv * ur;
+          lq += sur;
+          lx += dx * ui + a0 * sur;
+          ly += dy * ui + a1 * sur;
+          lz += dz * ui + a2 * sur;
+          le += (hv + alpha * sv) * ur + (a0 * dx + a1 * dy + a2 * dz) * ui;
+        }
+        aq += wk * lq;
+        ax += wk * lx;
+        ay += wk * ly;
+        az += wk * lz;
+        ae += wk * le;
       }
-      aq += wk * lq;
-      ax += wk * lx;
-      ay += wk * ly;
-      az += wk * lz;
-      ae += wk * le;
     }
   }
-  aq = warp_sum(aq);
-  ax = warp_sum(ax);
-  ay = warp_sum(ay);
-  az = warp_sum(az);
-  ae = warp_sum(ae);
-  if (lane == 0) {
-    double* p = T.part + 5LL * tg;
+  aq = half_sum(aq);
+  ax = half_sum(ax);
+  ay = half_sum(ay);
+  az = half_sum(az);
+  ae = half_sum(ae);
+  if (U.active && lane == 0) {
+    double* p = T.part + 5LL * U.tg;
     p[0] = aq;
     p[1] = ax;
     p[2] = ay;
@@ -112,20 +139,24 @@ __global__ void k_obs(const DevSys* __restrict__ sysv, const DevTraj* __restrict
 }
 
 void launch_obs(const DevSys* sys, const DevTraj* trj, const DevItem* items, const int* warp_prefix,
-                int n_traj, int total_warps, const int* step, int delta, int fixed_step, cudaStream_t st) {
+                int n_traj, int total_units, const int* step, int delta, int fixed_step, cudaStream_t st) {
   const int threads = 256;
-  const int blocks = (total_warps * 32 + threads - 1) / threads;
-  k_obs<<<blocks, threads, 0, st>>>(sys, trj, items, warp_prefix, n_traj, total_warps, step, delta,
-                                    fixed_step);
+  const int blocks = (total_units * 16 + threads - 1) / threads;
+  k_obs<<<blocks, threads, 0, st>>>(sys, trj, items, warp_prefix, n_traj, total_units, step, delta, fixed_step);
 }
 
 // ---------------------------------------------------------------------------
-// One CTA per trajectory: q_I = sum of its targets' partials, dq = q - Z,
-// eps = gamma dq (Eq. 10), J_a = -T_a / Omega (Eq. 14), E = E_band + dq.eps/2.
+// k_scc: kSccRows rows of eps per CTA, nblk CTAs per trajectory.
+// Every CTA rebuilds dq (cheap sums of the per-target partials) in shared
+// memory; CTA 0 also finishes J, the band energy, the charge record and the
+// checks; each CTA writes eps_I and dq_I eps_I for its rows; the last CTA to
+// arrive adds dq.eps/2 to the band energy in a fixed order.
 // ---------------------------------------------------------------------------
+constexpr int kSccThreads = 256;
+constexpr int kSccRows = 32;
+
 template <int NT>
 __device__ void block_sum5(double (&v)[5], double* sh) {
-  // sh: NT*5 doubles; fixed-tree reduction (deterministic)
   const int tid = threadIdx.x;
 #pragma unroll
   for (int i = 0; i < 5; ++i) sh[i * NT + tid] = v[i];
@@ -142,64 +173,86 @@ __device__ void block_sum5(double (&v)[5], double* sh) {
   __syncthreads();
 }
 
-constexpr int kSccThreads = 256;
-
-__global__ void __launch_bounds__(kSccThreads) k_scc(const DevSys* __restrict__ sysv, DevTraj* trj,
-                                                    int n_traj, const int* __restrict__ step, int stride,
+__global__ void __launch_bounds__(kSccThreads) k_scc(const DevSys* __restrict__ sysv, DevTraj* trj, int n_traj,
+                                                    int nblk, const int* __restrict__ step, int stride,
                                                     int fixed_step, int record) {
   extern __shared__ double sm[];  // [kSccThreads*5] reduction + [nat] dq
-  const int t = blockIdx.x;
+  __shared__ int s_last;
+  const int t = blockIdx.x / nblk, b = blockIdx.x % nblk;
   if (t >= n_traj) return;
   DevTraj& T = trj[t];
   const DevSys& S = sysv[T.sys];
+  const int myblk = (S.nat + kSccRows - 1) / kSccRows;
+  if (b >= myblk) return;
   const int n = fixed_step >= 0 ? fixed_step : *step;
   double* red = sm;
   double* dq = sm + 5 * kSccThreads;
   const int tid = threadIdx.x;
-  const bool rec_q = record && T.q && (n % stride == 0);
+  const bool rec_q = record && T.q && (n % stride == 0) && b == 0;
   double acc[5] = {0, 0, 0, 0, 0};  // sum q, Tx, Ty, Tz, Eband
   for (int I = tid; I < S.nat; I += kSccThreads) {
     double q = 0.0;
     for (int tg = S.atom_tgt0[I]; tg < S.atom_tgt0[I + 1]; ++tg) q += T.part[5LL * tg];
     dq[I] = q - S.z[I];
-    T.dq[I] = dq[I];
     acc[0] += q;
-    if (rec_q) T.q[(long long)(n / stride) * S.nat + I] = q;
-  }
-  for (int tg = tid; tg < S.n_tgt; tg += kSccThreads) {
-    acc[1] += T.part[5LL * tg + 1];
-    acc[2] += T.part[5LL * tg + 2];
-    acc[3] += T.part[5LL * tg + 3];
-    acc[4] += T.part[5LL * tg + 4];
+    if (b == 0) {
+      T.dq[I] = dq[I];
+      if (rec_q) T.q[(long long)(n / stride) * S.nat + I] = q;
+    }
   }
   __syncthreads();
-  block_sum5<kSccThreads>(acc, red);
-  // eps = gamma dq : one warp per row, fixed lane order
+  // eps rows of this CTA: one warp per row, lanes over K
   const int warp = tid >> 5, lane = tid & 31;
-  double escc = 0.0;
-  for (int I = warp; I < S.nat; I += kSccThreads / 32) {
+  const int r0 = b * kSccRows, r1 = min(S.nat, r0 + kSccRows);
+  for (int I = r0 + warp; I < r1; I += kSccThreads / 32) {
     double e = 0.0;
     const double* g = S.gamma + (long long)I * S.nat;
     for (int K = lane; K < S.nat; K += 32) e += g[K] * dq[K];
     e = warp_sum(e);
-    if (lane == 0) T.eps[I] = e;
-    escc += (lane == 0) ? dq[I] * e : 0.0;
-  }
-  double v5[5] = {escc, 0, 0, 0, 0};
-  block_sum5<kSccThreads>(v5, red);
-  if (tid == 0) {
-    const double J0 = -acc[1] / S.omega, J1 = -acc[2] / S.omega, J2 = -acc[3] / S.omega;
-    const double E = acc[4] + 0.5 * v5[0];
-    if (record) {
-      T.J[3LL * n] = J0;
-      T.J[3LL * n + 1] = J1;
-      T.J[3LL * n + 2] = J2;
-      T.E[n] = E;
+    if (lane == 0) {
+      T.eps[I] = e;
+      T.erow[I] = dq[I] * e;
     }
-    int st = 0;
-    if (!isfinite(J0) || !isfinite(J1) || !isfinite(J2) || !isfinite(E) || !isfinite(acc[0])) st |= ST_NONFINITE;
-    if (fabs(acc[0] - S.nel) > 1e-6 * fmax(1.0, S.nel)) st |= ST_DRIFT;
-    if (st) atomicOr(T.status, st);
+  }
+  if (b == 0) {
+    for (int tg = tid; tg < S.n_tgt; tg += kSccThreads) {
+      acc[1] += T.part[5LL * tg + 1];
+      acc[2] += T.part[5LL * tg + 2];
+      acc[3] += T.part[5LL * tg + 3];
+      acc[4] += T.part[5LL * tg + 4];
+    }
+    block_sum5<kSccThreads>(acc, red);
+    if (tid == 0) {
+      const double J0 = -acc[1] / S.omega, J1 = -acc[2] / S.omega, J2 = -acc[3] / S.omega;
+      if (record) {
+        T.J[3LL * n] = J0;
+        T.J[3LL * n + 1] = J1;
+        T.J[3LL * n + 2] = J2;
+      }
+      *T.eband = acc[4];
+      int st = 0;
+      if (!isfinite(J0) || !isfinite(J1) || !isfinite(J2) || !isfinite(acc[0])) st |= ST_NONFINITE;
+      if (fabs(acc[0] - S.nel) > 1e-6 * fmax(1.0, S.nel)) st |= ST_DRIFT;
+      if (st) atomicOr(T.status, st);
+    }
+  }
+  // last CTA of this trajectory: E = E_band + dq.eps / 2 in a fixed order
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    s_last = (atomicAdd(T.ticket, 1) == myblk - 1);
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  double v[5] = {0, 0, 0, 0, 0};
+  for (int I = tid; I < S.nat; I += kSccThreads) v[0] += T.erow[I];
+  block_sum5<kSccThreads>(v, red);
+  if (tid == 0) {
+    const double E = *T.eband + 0.5 * v[0];
+    if (record) T.E[n] = E;
+    if (!isfinite(E)) atomicOr(T.status, ST_NONFINITE);
+    *T.ticket = 0;
   }
 }
 
@@ -213,30 +266,85 @@ int scc_configure(int max_nat) {
 
 void launch_scc(const DevSys* sys, DevTraj* trj, int n_traj, const int* step, int stride, int fixed_step,
                 int record, int max_nat, cudaStream_t st) {
+  const int nblk = (max_nat + kSccRows - 1) / kSccRows;
   const size_t sm = sizeof(double) * (5 * kSccThreads + (size_t)max_nat);
-  k_scc<<<n_traj, kSccThreads, sm, st>>>(sys, trj, n_traj, step, stride, fixed_step, record);
+  k_scc<<<n_traj * nblk, kSccThreads, sm, st>>>(sys, trj, n_traj, nblk, step, stride, fixed_step, record);
 }
 
 // ---------------------------------------------------------------------------
-// Phase build: H_k(t)_{mu nu} = sum_images e^{-ik.L} v_{mu nu}(L) with
+// Phase build, FP64 path: H_k(t)_{mu nu} = sum_images e^{-ik.L} v_{mu nu}(L) with
 //   plain: v = H0 + (alpha + (eps_I + eps_J)/2) S + (i/c) A.dS        (Eqs. 9-12)
-//   delta: H without alpha (its commutator vanishes, Eq. 3 remark) and
+//   delta: H without alpha (its commutator vanishes, remark after Eq. 3) and
 //          dH = ((eps_I-eps0_I) + (eps_J-eps0_J))/2 S + (i/c) A.dS.
-// The split form stores the embedded real matrix [[Re, Im], [-Im, Re]] of H
-// and dH as BF16 hi/lo pieces, the B operand of the first product.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void split_bf16(double x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
-  hi = __double2bfloat16(x);
-  lo = __double2bfloat16(x - (double)__bfloat162float(hi));
+__global__ void __launch_bounds__(256) k_phase(const DevSys* __restrict__ sysv, const DevTraj* __restrict__ trj,
+                                               const DevItem* __restrict__ items, const int* __restrict__ wpre,
+                                               int n_traj, int total, const int* __restrict__ step, int mode,
+                                               int fixed_step) {
+  const Unit U = unit_of(wpre, n_traj, total);
+  if (!U.active) return;
+  const int lane = threadIdx.x & 15;
+  const DevTraj& T = trj[U.t];
+  const DevSys& S = sysv[T.sys];
+  const int n = fixed_step >= 0 ? fixed_step : *step;
+  double A0 = 0.0, A1 = 0.0, A2 = 0.0;
+  if (T.A) {
+    A0 = T.A[3 * n];
+    A1 = T.A[3 * n + 1];
+    A2 = T.A[3 * n + 2];
+  }
+  const double ic = 1.0 / kLight;
+  const double alpha = (A0 * A0 + A1 * A1 + A2 * A2) * 0.5 * ic * ic;
+  const int I = S.tgt_I[U.tg], J = S.tgt_J[U.tg];
+  const int oi = S.orb_off[I], ni = S.orb_off[I + 1] - oi;
+  const int oj = S.orb_off[J], nj = S.orb_off[J + 1] - oj;
+  const int nel = ni * nj;
+  const int g0 = S.tgt_img0[U.tg], g1 = S.tgt_img0[U.tg + 1];
+  const double ebar = 0.5 * (T.eps[I] + T.eps[J]);
+  const double beta = (mode == PH_FP64_PLAIN) ? alpha + ebar : ebar;
+  const double dbeta = (mode == PH_FP64_PLAIN) ? 0.0 : 0.5 * ((T.eps[I] - S.eps0[I]) + (T.eps[J] - S.eps0[J]));
+  for (int k = 0; k < S.nk; ++k) {
+    const DevItem& it = items[T.item0 + k];
+    for (int e = lane; e < nel; e += 16) {
+      const int a = e / nj, b = e - a * nj;
+      const long long idx = (long long)(oi + a) * S.Np + (oj + b);
+      double hr = 0.0, hi = 0.0, dr = 0.0, di = 0.0;
+      for (int g = g0; g < g1; ++g) {
+        const long long off = S.img_off[g] + e;
+        const double sv = S.s[off], hv = S.h0[off];
+        const double adS = (A0 * S.ds[off] + A1 * S.ds[S.ds_stride + off] + A2 * S.ds[2 * S.ds_stride + off]) * ic;
+        const double2 ph = S.phase[(long long)k * S.n_blk + S.img_blk[g]];
+        const double vr = hv + beta * sv;  // v = vr + i adS
+        hr += ph.x * vr - ph.y * adS;
+        hi += ph.x * adS + ph.y * vr;
+        const double wr = dbeta * sv;       // dv = wr + i adS
+        dr += ph.x * wr - ph.y * adS;
+        di += ph.x * adS + ph.y * wr;
+      }
+      it.H[idx] = make_double2(hr, hi);
+      if (mode == PH_FP64_DELTA) it.dH[idx] = make_double2(dr, di);
+    }
+  }
 }
 
-__device__ __forceinline__ void store_emb(__nv_bfloat16* base, int Np, int r, int c, double re, double im) {
-  // base -> piece 0; piece 1 at + 4 Np^2
+void launch_phase(const DevSys* sys, const DevTraj* trj, const DevItem* items, const int* warp_prefix,
+                  int n_traj, int total_units, const int* step, int mode, int fixed_step, cudaStream_t st) {
+  const int threads = 256;
+  const int blocks = (total_units * 16 + threads - 1) / threads;
+  k_phase<<<blocks, threads, 0, st>>>(sys, trj, items, warp_prefix, n_traj, total_units, step, mode, fixed_step);
+}
+
+// ---------------------------------------------------------------------------
+// Phase build, split form: the delta-form H and dH summed in FP32 and stored
+// as the embedded real matrix [[Re, Im], [-Im, Re]] in BF16 hi/lo pieces, the
+// B operand of the first product.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void store_emb_f(__nv_bfloat16* base, int Np, int r, int c, float re, float im) {
   const long long P = 4LL * Np * Np;
   const long long ld = 2LL * Np;
-  __nv_bfloat16 rh, rl, ih, il;
-  split_bf16(re, rh, rl);
-  split_bf16(im, ih, il);
+  const __nv_bfloat16 rh = __float2bfloat16_rn(re), ih = __float2bfloat16_rn(im);
+  const __nv_bfloat16 rl = __float2bfloat16_rn(re - __bfloat162float(rh));
+  const __nv_bfloat16 il = __float2bfloat16_rn(im - __bfloat162float(ih));
   const long long i00 = (long long)r * ld + c;
   const long long i01 = (long long)r * ld + Np + c;
   const long long i10 = (long long)(Np + r) * ld + c;
@@ -251,69 +359,58 @@ __device__ __forceinline__ void store_emb(__nv_bfloat16* base, int Np, int r, in
   base[P + i11] = rl;
 }
 
-__global__ void k_phase(const DevSys* __restrict__ sysv, const DevTraj* __restrict__ trj,
-                        const DevItem* __restrict__ items, const int* __restrict__ wpre, int n_traj,
-                        int total, const int* __restrict__ step, int mode, int fixed_step) {
-  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (w >= total) return;
-  const int t = find_traj(wpre, n_traj, w);
-  const int tg = w - wpre[t];
-  const DevTraj& T = trj[t];
+__global__ void __launch_bounds__(256) k_phase_split(const DevSys* __restrict__ sysv,
+                                                     const DevTraj* __restrict__ trj,
+                                                     const DevItem* __restrict__ items,
+                                                     const int* __restrict__ wpre, int n_traj, int total,
+                                                     const int* __restrict__ step) {
+  const Unit U = unit_of(wpre, n_traj, total);
+  if (!U.active) return;
+  const int lane = threadIdx.x & 15;
+  const DevTraj& T = trj[U.t];
   const DevSys& S = sysv[T.sys];
-  const int n = fixed_step >= 0 ? fixed_step : *step;
-  double A0 = 0.0, A1 = 0.0, A2 = 0.0;
+  const int n = *step;
+  float a0 = 0.f, a1 = 0.f, a2 = 0.f;
   if (T.A) {
-    A0 = T.A[3 * n];
-    A1 = T.A[3 * n + 1];
-    A2 = T.A[3 * n + 2];
+    a0 = (float)(T.A[3 * n] / kLight);
+    a1 = (float)(T.A[3 * n + 1] / kLight);
+    a2 = (float)(T.A[3 * n + 2] / kLight);
   }
-  const double ic = 1.0 / kLight;
-  const double alpha = (A0 * A0 + A1 * A1 + A2 * A2) * 0.5 * ic * ic;
-  const int I = S.tgt_I[tg], J = S.tgt_J[tg];
+  const int I = S.tgt_I[U.tg], J = S.tgt_J[U.tg];
   const int oi = S.orb_off[I], ni = S.orb_off[I + 1] - oi;
   const int oj = S.orb_off[J], nj = S.orb_off[J + 1] - oj;
   const int nel = ni * nj;
-  const int g0 = S.tgt_img0[tg], g1 = S.tgt_img0[tg + 1];
-  const double ebar = 0.5 * (T.eps[I] + T.eps[J]);
-  const double beta = (mode == PH_FP64_PLAIN) ? alpha + ebar : ebar;
-  const double dbeta = (mode == PH_FP64_PLAIN) ? 0.0 : 0.5 * ((T.eps[I] - S.eps0[I]) + (T.eps[J] - S.eps0[J]));
-  for (int e = lane; e < nel; e += 32) {
-    const int a = e / nj, b = e - a * nj;
-    const long long idx = (long long)(oi + a) * S.Np + (oj + b);
-    for (int k = 0; k < S.nk; ++k) {
-      double hr = 0.0, hi = 0.0, dr = 0.0, di = 0.0;
+  const int g0 = S.tgt_img0[U.tg], g1 = S.tgt_img0[U.tg + 1];
+  const float beta = (float)(0.5 * (T.eps[I] + T.eps[J]));
+  const float dbeta = (float)(0.5 * ((T.eps[I] - S.eps0[I]) + (T.eps[J] - S.eps0[J])));
+  for (int k = 0; k < S.nk; ++k) {
+    const DevItem& it = items[T.item0 + k];
+    for (int e = lane; e < nel; e += 16) {
+      const int a = e / nj, b = e - a * nj;
+      float hr = 0.f, hi = 0.f, dr = 0.f, di = 0.f;
       for (int g = g0; g < g1; ++g) {
-        const int blk = S.img_blk[g];
-        const long long off = S.blk_off[blk] + e;
-        const double sv = S.s[off], hv = S.h0[off];
-        const double adS = (A0 * S.ds[off] + A1 * S.ds[S.ds_stride + off] + A2 * S.ds[2 * S.ds_stride + off]) * ic;
-        const double2 ph = S.phase[(long long)k * S.n_blk + blk];
-        const double vr = hv + beta * sv;  // v = vr + i adS
+        const long long off = S.img_off[g] + e;
+        const float sv = S.sf[off], hv = S.h0f[off];
+        const float adS = a0 * S.dsf[off] + a1 * S.dsf[S.ds_stride + off] + a2 * S.dsf[2 * S.ds_stride + off];
+        const float2 ph = S.phasef[(long long)k * S.n_blk + S.img_blk[g]];
+        const float vr = hv + beta * sv;
         hr += ph.x * vr - ph.y * adS;
         hi += ph.x * adS + ph.y * vr;
-        const double wr = dbeta * sv;       // dv = wr + i adS
+        const float wr = dbeta * sv;
         dr += ph.x * wr - ph.y * adS;
         di += ph.x * adS + ph.y * wr;
       }
-      const DevItem& it = items[T.item0 + k];
-      if (mode == PH_SPLIT) {
-        store_emb(it.Hemb_p, S.Np, oi + a, oj + b, hr, hi);
-        store_emb(it.dHemb_p, S.Np, oi + a, oj + b, dr, di);
-      } else {
-        it.H[idx] = make_double2(hr, hi);
-        if (mode == PH_FP64_DELTA) it.dH[idx] = make_double2(dr, di);
-      }
+      store_emb_f(it.Hemb_p, S.Np, oi + a, oj + b, hr, hi);
+      store_emb_f(it.dHemb_p, S.Np, oi + a, oj + b, dr, di);
     }
   }
 }
 
-void launch_phase(const DevSys* sys, const DevTraj* trj, const DevItem* items, const int* warp_prefix,
-                  int n_traj, int total_warps, const int* step, int mode, int fixed_step, cudaStream_t st) {
+void launch_phase_split(const DevSys* sys, const DevTraj* trj, const DevItem* items, const int* warp_prefix,
+                        int n_traj, int total_units, const int* step, cudaStream_t st) {
   const int threads = 256;
-  const int blocks = (total_warps * 32 + threads - 1) / threads;
-  k_phase<<<blocks, threads, 0, st>>>(sys, trj, items, warp_prefix, n_traj, total_warps, step, mode,
-                                      fixed_step);
+  const int blocks = (total_units * 16 + threads - 1) / threads;
+  k_phase_split<<<blocks, threads, 0, st>>>(sys, trj, items, warp_prefix, n_traj, total_units, step);
 }
 
 // ---------------------------------------------------------------------------
@@ -337,7 +434,7 @@ __global__ void k_bloch_setup(const DevSys* __restrict__ sysv, int s_idx, int k,
     double xr = 0.0, xi = 0.0;
     for (int g = S.tgt_img0[tg]; g < S.tgt_img0[tg + 1]; ++g) {
       const int blk = S.img_blk[g];
-      const long long off = S.blk_off[blk] + e;
+      const long long off = S.img_off[g] + e;
       const double v = mode == 1 ? S.h0[off] + beta * S.s[off] : S.s[off];
       const double2 ph = S.phase[(long long)k * S.n_blk + blk];
       xr += ph.x * v;
@@ -365,9 +462,8 @@ __global__ void k_mulliken_setup(const DevSys* __restrict__ sysv, int s_idx, con
       const double2 d = D[k * NN + idx];
       double l = 0.0;
       for (int g = S.tgt_img0[tg]; g < S.tgt_img0[tg + 1]; ++g) {
-        const int blk = S.img_blk[g];
-        const double2 ph = S.phase[(long long)k * S.n_blk + blk];
-        l += S.s[S.blk_off[blk] + e] * (d.x * ph.x + d.y * ph.y);
+        const double2 ph = S.phase[(long long)k * S.n_blk + S.img_blk[g]];
+        l += S.s[S.img_off[g] + e] * (d.x * ph.x + d.y * ph.y);
       }
       acc += S.wk[k] * l;
     }

@@ -102,7 +102,6 @@ __device__ __forceinline__ void split_bf16_d(double x, __nv_bfloat16& hi, __nv_b
   lo = __double2bfloat16(x - (double)__bfloat162float(hi));
 }
 
-template <bool XF32>
 __global__ void __launch_bounds__(256) k_leap(const LeapItem* __restrict__ items, const int* step,
                                               double dt, int* counter, int* step_rw) {
   __shared__ double2 Xa[LT][LT + 1];
@@ -127,17 +126,9 @@ __global__ void __launch_bounds__(256) k_leap(const LeapItem* __restrict__ items
     for (int r = ty; r < LT; r += 8) {
       const long long ia = (long long)(bi * LT + r) * Np + bj * LT + tx;
       const long long ib = (long long)(bj * LT + r) * Np + bi * LT + tx;
-      if (XF32) {
-        const float* X = (const float*)it.X;
-        const long long ra = (long long)(bi * LT + r) * 2 * Np + bj * LT + tx;
-        const long long rb = (long long)(bj * LT + r) * 2 * Np + bi * LT + tx;
-        Xa[r][tx] = make_double2(X[ra], X[ra + Np]);
-        Xb[r][tx] = make_double2(X[rb], X[rb + Np]);
-      } else {
-        const double2* X = (const double2*)it.X;
-        Xa[r][tx] = X[ia];
-        Xb[r][tx] = X[ib];
-      }
+      const double2* X = (const double2*)it.X;
+      Xa[r][tx] = X[ia];
+      Xb[r][tx] = X[ib];
     }
   }
   __syncthreads();
@@ -197,13 +188,117 @@ __global__ void __launch_bounds__(256) k_leap(const LeapItem* __restrict__ items
 
 void launch_leap(const LeapItem* items, int n_items, int Np_max, int x_f32, const int* step, double dt,
                  int* counter, int* step_rw, cudaStream_t st) {
+  (void)x_f32;
   const int nt = Np_max / LT;
   dim3 grid(nt * (nt + 1) / 2, n_items);
   dim3 block(LT, 8);
-  if (x_f32)
-    k_leap<true><<<grid, block, 0, st>>>(items, step, dt, counter, step_rw);
-  else
-    k_leap<false><<<grid, block, 0, st>>>(items, step, dt, counter, step_rw);
+  k_leap<<<grid, block, 0, st>>>(items, step, dt, counter, step_rw);
+}
+
+// ---------------------------------------------------------------------------
+// Leapfrog of the split form: X (FP32 planar) and R0 (FP32 planar) give
+// dD/dt in FP32 with the same mirror-exact operations as k_leap; only the
+// master update dD_{n+1} = dD_{n-1} + 2 dt dD/dt is FP64 (GB300's FP64 rate is
+// low, so FP64 is kept to the accumulation that needs it).  The BF16 hi/lo
+// pieces of the new level (A operand of the next first product) are split
+// from its FP32 rounding.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_leap_split(const LeapItem* __restrict__ items, const int* step, double dt,
+                                                    int* counter, int* step_rw) {
+  __shared__ float2 Xa[LT][LT + 1];
+  __shared__ float2 Xb[LT][LT + 1];
+  const LeapItem& it = items[blockIdx.y];
+  const int Np = it.Np;
+  const int nt = Np / LT;
+  const int n = *step;
+  int p = blockIdx.x, bi = 0;
+  const int npairs = nt * (nt + 1) / 2;
+  const bool active = p < npairs;
+  if (active) {
+    while (p >= nt - bi) {
+      p -= nt - bi;
+      ++bi;
+    }
+  }
+  const int bj = bi + p;
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  const float* X = (const float*)it.X;
+  if (active) {
+    for (int r = ty; r < LT; r += 8) {
+      const long long ra = (long long)(bi * LT + r) * 2 * Np + bj * LT + tx;
+      const long long rb = (long long)(bj * LT + r) * 2 * Np + bi * LT + tx;
+      Xa[r][tx] = make_float2(X[ra], X[ra + Np]);
+      Xb[r][tx] = make_float2(X[rb], X[rb + Np]);
+    }
+  }
+  __syncthreads();
+  if (active) {
+    const int cur = n & 1, nxt = cur ^ 1;
+    const bool euler = (n == 0);
+    const double coef = euler ? dt : 2.0 * dt;
+    const double2* base = euler ? it.D[cur] : it.D[nxt];
+    const long long P = 2LL * Np * Np;
+    for (int half = 0; half < (bi == bj ? 1 : 2); ++half) {
+      const int gi0 = half == 0 ? bi : bj, gj0 = half == 0 ? bj : bi;
+      for (int r = ty; r < LT; r += 8) {
+        const float2 xij = half == 0 ? Xa[r][tx] : Xb[r][tx];
+        const float2 xji = half == 0 ? Xb[tx][r] : Xa[tx][r];
+        const long long idx = (long long)(gi0 * LT + r) * Np + gj0 * LT + tx;
+        const long long pr = (long long)(gi0 * LT + r) * 2 * Np + gj0 * LT + tx;
+        float dr = xij.y + xji.y;
+        float di = -(xij.x - xji.x);
+        if (it.R0f) {
+          dr = it.R0f[pr] + dr;
+          di = it.R0f[pr + Np] + di;
+        }
+        const double2 b = base[idx];
+        const double2 v = make_double2(fma(coef, (double)dr, b.x), fma(coef, (double)di, b.y));
+        it.D[nxt][idx] = v;
+        const float fr = (float)v.x, fi = (float)v.y;
+        const __nv_bfloat16 rh = __float2bfloat16_rn(fr), ih = __float2bfloat16_rn(fi);
+        it.pieces[pr] = rh;
+        it.pieces[P + pr] = __float2bfloat16_rn(fr - __bfloat162float(rh));
+        it.pieces[pr + Np] = ih;
+        it.pieces[P + pr + Np] = __float2bfloat16_rn(fi - __bfloat162float(ih));
+      }
+    }
+  }
+  if (counter) {
+    __syncthreads();
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+      __threadfence();
+      const int total = gridDim.x * gridDim.y;
+      const int ticket = atomicAdd(counter, 1);
+      if (ticket == total - 1) {
+        *counter = 0;
+        *step_rw = n + 1;
+        __threadfence();
+      }
+    }
+  }
+}
+
+void launch_leap_split(const LeapItem* items, int n_items, int Np_max, const int* step, double dt, int* counter,
+                       int* step_rw, cudaStream_t st) {
+  const int nt = Np_max / LT;
+  dim3 grid(nt * (nt + 1) / 2, n_items);
+  dim3 block(LT, 8);
+  k_leap_split<<<grid, block, 0, st>>>(items, step, dt, counter, step_rw);
+}
+
+// complex128 row-major Np x Np -> FP32 planar [Re(row) | Im(row)]
+__global__ void k_to_planar_f32(const double2* src, float* dst, int Np) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)Np * Np) return;
+  const int i = idx / Np, j = idx % Np;
+  const double2 v = src[idx];
+  dst[(long long)i * 2 * Np + j] = (float)v.x;
+  dst[(long long)i * 2 * Np + Np + j] = (float)v.y;
+}
+
+void launch_to_planar_f32(const double2* src, float* dst, int Np, cudaStream_t st) {
+  const long long tot = (long long)Np * Np;
+  k_to_planar_f32<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(src, dst, Np);
 }
 
 // ---------------------------------------------------------------------------

@@ -48,6 +48,7 @@ struct HostSys {
   double* eps0 = nullptr;
   __nv_bfloat16* Sinv_p = nullptr;
   __nv_bfloat16* D0_p = nullptr;
+  float* R0f = nullptr;
   std::vector<double> dq0_h, eps0_h;
   bool density_set = false;
   std::vector<int> trajs;  // trajectories of this system
@@ -64,6 +65,9 @@ struct HostTraj {
   double* dq = nullptr;
   double* eps = nullptr;
   double* part = nullptr;
+  double* erow = nullptr;
+  double* eband = nullptr;
+  int* ticket = nullptr;
   int* status = nullptr;
 };
 
@@ -325,6 +329,12 @@ int prepare_system(vgtb_ctx* ctx, int si, const vgtb_system& s, HostSys& h, DevS
   d.tgt_img0 = pi;
   TRY(upload(ctx, &pi, h.img_blk.data(), h.img_blk.size()));
   d.img_blk = pi;
+  {
+    std::vector<long long> io(h.img_blk.size());
+    for (size_t g = 0; g < io.size(); ++g) io[g] = h.blk_off[h.img_blk[g]];
+    TRY(upload(ctx, &pl, io.data(), io.size()));
+    d.img_off = pl;
+  }
   TRY(upload(ctx, &pl, h.blk_off.data(), h.blk_off.size()));
   d.blk_off = pl;
   TRY(upload(ctx, &pd, s.h0, (size_t)tot));
@@ -336,6 +346,25 @@ int prepare_system(vgtb_ctx* ctx, int si, const vgtb_system& s, HostSys& h, DevS
   d.ds_stride = tot;
   TRY(upload(ctx, &pz, ph.data(), ph.size()));
   d.phase = pz;
+  if (ctx->split) {
+    // FP32 copies for the split form's phase build
+    std::vector<float> f(3 * (size_t)tot);
+    float* pf;
+    for (long long i = 0; i < tot; ++i) f[i] = (float)s.h0[i];
+    TRY(upload(ctx, &pf, f.data(), (size_t)tot));
+    d.h0f = pf;
+    for (long long i = 0; i < tot; ++i) f[i] = (float)s.s[i];
+    TRY(upload(ctx, &pf, f.data(), (size_t)tot));
+    d.sf = pf;
+    for (long long i = 0; i < 3 * tot; ++i) f[i] = (float)s.ds[i];
+    TRY(upload(ctx, &pf, f.data(), 3 * (size_t)tot));
+    d.dsf = pf;
+    std::vector<float2> pff(ph.size());
+    for (size_t i = 0; i < ph.size(); ++i) pff[i] = make_float2((float)ph[i].x, (float)ph[i].y);
+    float2* pf2;
+    TRY(upload(ctx, &pf2, pff.data(), pff.size()));
+    d.phasef = pf2;
+  }
   TRY(upload(ctx, &pd, h.wk.data(), h.wk.size()));
   d.wk = pd;
   TRY(upload(ctx, &pi, h.atom_tgt0.data(), h.atom_tgt0.size()));
@@ -349,6 +378,7 @@ int prepare_system(vgtb_ctx* ctx, int si, const vgtb_system& s, HostSys& h, DevS
   if (ctx->split) {
     TRY(dalloc(ctx, &h.Sinv_p, 4 * NN * h.nk));
     TRY(dalloc(ctx, &h.D0_p, 4 * NN * h.nk));
+    TRY(dalloc(ctx, &h.R0f, 2 * NN * h.nk));
   }
   d.Sinv = h.Sinv;
   d.D0 = h.D0;
@@ -357,6 +387,7 @@ int prepare_system(vgtb_ctx* ctx, int si, const vgtb_system& s, HostSys& h, DevS
   d.eps0 = h.eps0;
   d.Sinv_p = h.Sinv_p;
   d.D0_p = h.D0_p;
+  d.R0f = h.R0f;
   return VGTB_OK;
 }
 
@@ -623,6 +654,7 @@ int finish_density(vgtb_ctx* ctx, int si) {
     for (int k = 0; k < h.nk; ++k) {
       launch_split_planar(h.D0 + k * NN, h.D0_p + 4 * NN * k, h.N, h.Np, ctx->stream);
       launch_split_planar(h.Sinv + k * NN, h.Sinv_p + 4 * NN * k, h.N, h.Np, ctx->stream);
+      launch_to_planar_f32(h.R0 + k * NN, h.R0f + 2 * NN * k, h.Np, ctx->stream);
     }
     CK(cudaGetLastError());
   }
@@ -666,6 +698,9 @@ int upload_traj_table(vgtb_ctx* ctx) {
     d.dq = h.dq;
     d.eps = h.eps;
     d.part = h.part;
+    d.erow = h.erow;
+    d.eband = h.eband;
+    d.ticket = h.ticket;
     d.status = h.status;
   }
   CK(cudaMemcpyAsync(ctx->d_trj, dt.data(), sizeof(DevTraj) * dt.size(), cudaMemcpyHostToDevice, ctx->stream));
@@ -698,8 +733,11 @@ int enqueue_step(vgtb_ctx* ctx, cudaEvent_t* ev) {
   if (ev) CK(cudaEventRecordWithFlags(ev[1], st, evflag));
   launch_scc(ctx->d_sys, ctx->d_trj, nt, ctx->d_step, stride, -1, 1, ctx->max_nat, st);
   if (ev) CK(cudaEventRecordWithFlags(ev[2], st, evflag));
-  const int mode = ctx->split ? PH_SPLIT : (ctx->delta ? PH_FP64_DELTA : PH_FP64_PLAIN);
-  launch_phase(ctx->d_sys, ctx->d_trj, ctx->d_items, ctx->d_wpre, nt, ctx->total_warps, ctx->d_step, mode, -1, st);
+  if (ctx->split)
+    launch_phase_split(ctx->d_sys, ctx->d_trj, ctx->d_items, ctx->d_wpre, nt, ctx->total_warps, ctx->d_step, st);
+  else
+    launch_phase(ctx->d_sys, ctx->d_trj, ctx->d_items, ctx->d_wpre, nt, ctx->total_warps, ctx->d_step,
+                 ctx->delta ? PH_FP64_DELTA : PH_FP64_PLAIN, -1, st);
   if (ev) CK(cudaEventRecordWithFlags(ev[3], st, evflag));
   if (ctx->split) {
     TRY(tc_launch(ctx->tc1, st) == 0 ? VGTB_OK : fail(ctx, VGTB_E_CUDA, "tcgen05 product 1 launch failed"));
@@ -711,8 +749,12 @@ int enqueue_step(vgtb_ctx* ctx, cudaEvent_t* ev) {
     launch_gemm_f64(ctx->d_g2, ctx->n_items, ctx->max_Np, ctx->max_Np, ctx->d_step, st);
   }
   if (ev) CK(cudaEventRecordWithFlags(ev[5], st, evflag));
-  launch_leap(ctx->d_leap, ctx->n_items, ctx->max_Np, ctx->split ? 1 : 0, ctx->d_step, ctx->sys[0].dt,
-              ctx->d_counter, ctx->d_step, st);
+  if (ctx->split)
+    launch_leap_split(ctx->d_leap, ctx->n_items, ctx->max_Np, ctx->d_step, ctx->sys[0].dt, ctx->d_counter,
+                      ctx->d_step, st);
+  else
+    launch_leap(ctx->d_leap, ctx->n_items, ctx->max_Np, 0, ctx->d_step, ctx->sys[0].dt, ctx->d_counter,
+                ctx->d_step, st);
   if (ev) CK(cudaEventRecordWithFlags(ev[6], st, evflag));
   CK(cudaGetLastError());
   return VGTB_OK;
@@ -911,6 +953,9 @@ int vgtb_create_batch(vgtb_ctx** out, int n_sys, const vgtb_system* sys, int n_t
     if ((rc = dalloc(ctx, &T.dq, h.nat))) return bail(rc);
     if ((rc = dalloc(ctx, &T.eps, h.nat))) return bail(rc);
     if ((rc = dalloc(ctx, &T.part, 5 * (size_t)h.n_tgt))) return bail(rc);
+    if ((rc = dalloc(ctx, &T.erow, h.nat))) return bail(rc);
+    if ((rc = dalloc(ctx, &T.eband, 1))) return bail(rc);
+    if ((rc = dalloc(ctx, &T.ticket, 1))) return bail(rc);
     if ((rc = dalloc(ctx, &T.status, 1))) return bail(rc);
   }
   ctx->n_items = (int)ctx->items_h.size();
@@ -955,7 +1000,8 @@ int vgtb_create_batch(vgtb_ctx** out, int n_sys, const vgtb_system* sys, int n_t
     g2[i] = b;
     LeapItem l{};
     l.X = ctx->split ? (const void*)it.Xf : (const void*)it.X;
-    l.R0 = ctx->delta ? h.R0 + it.k * NN : nullptr;
+    l.R0 = (ctx->delta && !ctx->split) ? h.R0 + it.k * NN : nullptr;
+    l.R0f = ctx->split ? h.R0f + 2 * NN * it.k : nullptr;
     l.D[0] = it.D[0];
     l.D[1] = it.D[1];
     l.pieces = it.dD_p;

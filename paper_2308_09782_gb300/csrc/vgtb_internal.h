@@ -38,6 +38,7 @@ struct DevSys {
   const int* tgt_J;        // [n_tgt]
   const int* tgt_img0;     // [n_tgt+1] range into img_blk
   const int* img_blk;      // [n_img] block index of each image
+  const long long* img_off;// [n_img] value offset of each image's block
   const long long* blk_off;// [n_blk] offset of each block's values
   const double* h0;        // values
   const double* s;
@@ -53,6 +54,12 @@ struct DevSys {
   double* eps0;            // [nat] shift of D(0)
   __nv_bfloat16* Sinv_p;   // [nk][2][Np][2Np] split pieces (split form)
   __nv_bfloat16* D0_p;     // [nk][2][Np][2Np]
+  // split form only: FP32 copies for the phase build and the leapfrog derivative
+  const float* h0f;        // values as float
+  const float* sf;
+  const float* dsf;        // [3][ds_stride]
+  const float2* phasef;    // [nk][n_blk]
+  float* R0f;              // [nk][Np][2Np] planar
 };
 
 struct DevTraj {
@@ -67,6 +74,9 @@ struct DevTraj {
   double* dq;              // [nat] current dq
   double* eps;             // [nat] current eps
   double* part;            // [n_tgt][5] per-target partial sums
+  double* erow;            // [nat] dq_I eps_I (energy of the SCC term, per row)
+  double* eband;           // [1] band energy of the current level
+  int* ticket;             // [1] CTA arrival counter of k_scc (reset by the last CTA)
   int* status;
 };
 
@@ -88,7 +98,6 @@ struct DevItem {
 enum PhaseMode : int {
   PH_FP64_PLAIN = 0,   // H = H0 + (alpha + (eps_I+eps_J)/2) S + (i/c) A.dS  -> item.H
   PH_FP64_DELTA = 1,   // H without alpha -> item.H ; dH = ((deps_I+deps_J)/2) S + (i/c) A.dS -> item.dH
-  PH_SPLIT = 2,        // as PH_FP64_DELTA, written as embedded BF16 hi/lo pieces
 };
 
 // Launchers (all enqueue on `st`)
@@ -96,6 +105,9 @@ void launch_obs(const DevSys* sys, const DevTraj* trj, const DevItem* items, con
                 int n_traj, int total_warps, const int* step, int delta, int fixed_step, cudaStream_t st);
 void launch_scc(const DevSys* sys, DevTraj* trj, int n_traj, const int* step, int stride,
                 int fixed_step, int record, int max_nat, cudaStream_t st);
+void launch_phase_split(const DevSys* sys, const DevTraj* trj, const DevItem* items, const int* warp_prefix,
+                        int n_traj, int total_units, const int* step, cudaStream_t st);
+void launch_to_planar_f32(const double2* src, float* dst, int Np, cudaStream_t st);
 void launch_phase(const DevSys* sys, const DevTraj* trj, const DevItem* items, const int* warp_prefix,
                   int n_traj, int total_warps, const int* step, int mode, int fixed_step, cudaStream_t st);
 int scc_configure(int max_nat);
@@ -118,7 +130,8 @@ void launch_gemm_f64(const GemmF64Item* items, int n_items, int max_m, int max_n
 
 struct LeapItem {
   const void* X;           // FP64 interleaved (double2) or FP32 planar
-  const double2* R0;       // optional
+  const double2* R0;       // optional (FP64 path)
+  const float* R0f;        // optional (split path, FP32 planar)
   double2* D[2];
   __nv_bfloat16* pieces;   // optional [2][Np][2Np]
   int Np;
@@ -127,6 +140,8 @@ struct LeapItem {
 };
 void launch_leap(const LeapItem* items, int n_items, int Np_max, int x_f32, const int* step, double dt,
                  int* counter, int* step_rw, cudaStream_t st);
+void launch_leap_split(const LeapItem* items, int n_items, int Np_max, const int* step, double dt, int* counter,
+                       int* step_rw, cudaStream_t st);
 
 // helpers
 void launch_fill_hermitian_lower(double2* a, int n, int ld, cudaStream_t st);
