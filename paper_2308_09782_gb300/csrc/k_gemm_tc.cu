@@ -51,10 +51,11 @@ bool encode_map(CUtensorMap* m, const void* base, int cols, int rows, int batch,
 }
 
 struct Variant {
-  int bn, st;
+  int bn, st, streamk;
 };
-constexpr Variant kVariants[] = {{256, 2}, {128, 3}};
-constexpr int kNumVariants = 2;
+// tile width, pipeline stages, stream-K schedule (autotune candidates; the first is the default)
+constexpr Variant kVariants[] = {{256, 2, 0}, {256, 2, 1}, {128, 3, 0}, {128, 3, 1}};
+constexpr int kNumVariants = 4;
 
 template <int BN, int ST, int EPI>
 int smem_bytes() {
@@ -74,15 +75,12 @@ cudaError_t configure_t() {
 }
 
 cudaError_t launch_variant(const TcPlan* p, cudaStream_t st) {
-  if (p->epi == 0) {
-    if (p->variant == 0) return launch_t<256, 2, 0>(p, st);
-    return launch_t<128, 3, 0>(p, st);
-  }
-  if (p->variant == 0) return launch_t<256, 2, 1>(p, st);
-  return launch_t<128, 3, 1>(p, st);
+  const bool wide = kVariants[p->variant].bn == 256;
+  if (p->epi == 0) return wide ? launch_t<256, 2, 0>(p, st) : launch_t<128, 3, 0>(p, st);
+  return wide ? launch_t<256, 2, 1>(p, st) : launch_t<128, 3, 1>(p, st);
 }
 
-int variant_smem(int v) { return v == 0 ? smem_bytes<256, 2, 0>() : smem_bytes<128, 3, 0>(); }
+int variant_smem(int v) { return kVariants[v].bn == 256 ? smem_bytes<256, 2, 0>() : smem_bytes<128, 3, 0>(); }
 
 cudaError_t configure_all() {
   cudaError_t e;
@@ -128,6 +126,7 @@ static int build_one(const std::vector<TcSysView>& sys, const std::vector<DevIte
   std::vector<TcProb> probs;
   std::vector<int> local(sys.size(), 0);
   int tiles = 0;
+  long long iters = 0;
   for (const DevItem& it : items) {
     const TcSysView& v = sys[it.sys];
     TcProb pr{};
@@ -148,7 +147,10 @@ static int build_one(const std::vector<TcSysView>& sys, const std::vector<DevIte
       pr.b_b[0] = li;
       pr.out = it.Xf;
     }
+    pr.kt = (epi == 0 ? 2 : 1) * (2 * v.Np) / BK;
+    pr.iter0 = (int)iters;
     tiles += pr.tiles_m * pr.tiles_n;
+    iters += (long long)pr.tiles_m * pr.tiles_n * pr.kt;
     probs.push_back(pr);
   }
   if (cudaMalloc(&plan->d_probs, sizeof(TcProb) * probs.size()) != cudaSuccess ||
@@ -169,6 +171,20 @@ static int build_one(const std::vector<TcSysView>& sys, const std::vector<DevIte
   plan->P.timeout_ns = timeout_ns;
   plan->grid = std::min(tiles, nsm);
   plan->smem = variant_smem(variant);
+  // stream-K needs every CTA to own at least one k-iteration; otherwise fall back
+  if (kVariants[variant].streamk && iters >= 2LL * nsm) {
+    plan->grid = nsm;
+    plan->P.streamk = 1;
+    plan->P.total_iters = iters;
+    if (cudaMalloc(&plan->d_ws, sizeof(float) * (size_t)nsm * BM * BNv) != cudaSuccess ||
+        cudaMalloc(&plan->d_flags, sizeof(int) * nsm) != cudaSuccess) {
+      *msg = "cudaMalloc failed for the stream-K workspace";
+      return -1;
+    }
+    cudaMemset(plan->d_flags, 0, sizeof(int) * nsm);
+    plan->P.ws = plan->d_ws;
+    plan->P.flags = plan->d_flags;
+  }
   return 0;
 }
 
@@ -252,6 +268,8 @@ void tc_destroy_plan(TcPlan* p) {
   if (!p) return;
   if (p->d_probs) cudaFree(p->d_probs);
   if (p->d_err) cudaFree(p->d_err);
+  if (p->d_ws) cudaFree(p->d_ws);
+  if (p->d_flags) cudaFree(p->d_flags);
   delete p;
 }
 

@@ -36,6 +36,8 @@ struct TcProb {
   int a_b[2], b_b[2];  // batch coordinate of each segment's A / B operand
   int tiles_m, tiles_n, tile0, Np;
   void* out;
+  int kt;              // k-iterations per tile (stream-K schedule)
+  int iter0;           // first global k-iteration of the problem (stream-K schedule)
 };
 
 struct TcParams {
@@ -45,12 +47,22 @@ struct TcParams {
   int n_prob, total_tiles, nseg;
   int* err;
   long long timeout_ns;
+  // stream-K schedule (streamk != 0): CTA c owns the global k-iterations
+  // [total_iters c / G, total_iters (c+1) / G); a tile shared by several CTAs
+  // is finished by the CTA holding its k = 0 part, after adding the FP32
+  // partials that the others left in ws[cta] and announced in flags[cta].
+  int streamk;
+  long long total_iters;
+  float* ws;           // [G][BM][BN]
+  int* flags;          // [G], 1 = partial ready (reset to 0 by the finishing CTA)
 };
 
 struct TcPlan {
   TcParams P;
   TcProb* d_probs = nullptr;
   int* d_err = nullptr;
+  float* d_ws = nullptr;
+  int* d_flags = nullptr;
   int grid = 0, smem = 0, variant = 0, epi = 0;
 };
 
@@ -167,6 +179,53 @@ __device__ __forceinline__ int find_prob(const TcProb* probs, int n, int t, int 
   return p;
 }
 
+// Work units: classic mode walks whole tiles t = blockIdx.x + i G; stream-K
+// mode walks this CTA's k-iteration range, split at tile boundaries.  Every
+// role of the CTA runs the same cursor, so they agree on the sequence.
+struct UnitCursor {
+  long long it, e;
+  int t_next, p;
+};
+
+__device__ __forceinline__ long long sk_start(const TcParams& P, int c) {
+  return P.total_iters * (long long)c / (long long)gridDim.x;
+}
+
+__device__ __forceinline__ void cursor_init(const TcParams& P, UnitCursor& u) {
+  u.p = 0;
+  u.t_next = blockIdx.x;
+  u.it = P.streamk ? sk_start(P, blockIdx.x) : 0;
+  u.e = P.streamk ? sk_start(P, blockIdx.x + 1) : 0;
+}
+
+// next unit: global tile t, its k-iterations [kb, ke) out of KT; false when done
+__device__ __forceinline__ bool cursor_next(const TcParams& P, UnitCursor& u, int& t, int& kb, int& ke, int& KT) {
+  if (P.streamk) {
+    if (u.it >= u.e) return false;
+    while (u.p + 1 < P.n_prob && P.probs[u.p + 1].iter0 <= u.it) ++u.p;
+    const TcProb& pr = P.probs[u.p];
+    KT = pr.kt;
+    const long long rel = u.it - pr.iter0;
+    const int local = (int)(rel / KT);
+    const long long tile_start = pr.iter0 + (long long)local * KT;
+    t = pr.tile0 + local;
+    kb = (int)(u.it - tile_start);
+    ke = (int)((u.e - tile_start) < KT ? (u.e - tile_start) : KT);
+    u.it = tile_start + ke;
+    return true;
+  }
+  if (u.t_next >= P.total_tiles) return false;
+  t = u.t_next;
+  u.t_next += gridDim.x;
+  u.p = find_prob(P.probs, P.n_prob, t, u.p);
+  KT = P.nseg * (2 * P.probs[u.p].Np) / BK;
+  kb = 0;
+  ke = KT;
+  return true;
+}
+
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
 // ----------------------------------------------------------------------------
 // the kernel
 // ----------------------------------------------------------------------------
@@ -182,7 +241,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcPa
   const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + ST), accf0 = smem_u32(bars + 2 * ST),
                  acce0 = smem_u32(bars + 2 * ST + 2), drain = smem_u32(bars + 2 * ST + 4);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * ST + 5);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);  // [0] abort, [1..2] epilogue ok
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   if (threadIdx.x == 0) {
@@ -209,37 +268,35 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcPa
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  const int G = gridDim.x;
-  const int kt_seg = 0;  // per-problem, computed below
-  (void)kt_seg;
+  volatile int* s_epi_ok = abort_flag + 1;  // indexed by unit parity
 
   if (warp == 0) {
     if (lane == 0) {
       // ---------------- TMA producer ----------------
-      int it = 0, p = 0;
+      int it = 0, t, kb, ke, KT;
       bool ok = true;
-      for (int t = blockIdx.x; ok && t < P.total_tiles; t += G) {
-        p = find_prob(P.probs, P.n_prob, t, p);
-        const TcProb& pr = P.probs[p];
+      UnitCursor cur;
+      cursor_init(P, cur);
+      while (ok && cursor_next(P, cur, t, kb, ke, KT)) {
+        const TcProb& pr = P.probs[cur.p];
         const int local = t - pr.tile0;
         const int mt = local % pr.tiles_m, nt = local / pr.tiles_m;
         const int kts = (2 * pr.Np) / BK;
-        for (int sg = 0; ok && sg < P.nseg; ++sg) {
+        for (int kk = kb; kk < ke; ++kk, ++it) {
+          const int sg = kk / kts, kt = kk - sg * kts;
           const CUtensorMap* ma = &P.mA[pr.sys][sg];
           const CUtensorMap* mb = &P.mB[pr.sys][sg];
-          for (int kt = 0; kt < kts; ++kt, ++it) {
-            const int s = it % ST, r = it / ST;
-            if (!mbar_wait(empty0 + 8 * s, (r & 1) ^ 1, P.timeout_ns, abort_flag, P.err)) {
-              ok = false;
-              break;
-            }
-            const uint32_t base = smem_u32(sm + s * STAGE);
-            mbar_expect_tx(full0 + 8 * s, STAGE);
-            tma_load_4d(base, ma, kt * BK, mt * BM, 0, pr.a_b[sg], full0 + 8 * s);
-            tma_load_4d(base + A_BYTES, ma, kt * BK, mt * BM, 1, pr.a_b[sg], full0 + 8 * s);
-            tma_load_4d(base + 2 * A_BYTES, mb, kt * BK, nt * BN, 0, pr.b_b[sg], full0 + 8 * s);
-            tma_load_4d(base + 2 * A_BYTES + B_BYTES, mb, kt * BK, nt * BN, 1, pr.b_b[sg], full0 + 8 * s);
+          const int s = it % ST, r = it / ST;
+          if (!mbar_wait(empty0 + 8 * s, (r & 1) ^ 1, P.timeout_ns, abort_flag, P.err)) {
+            ok = false;
+            break;
           }
+          const uint32_t base = smem_u32(sm + s * STAGE);
+          mbar_expect_tx(full0 + 8 * s, STAGE);
+          tma_load_4d(base, ma, kt * BK, mt * BM, 0, pr.a_b[sg], full0 + 8 * s);
+          tma_load_4d(base + A_BYTES, ma, kt * BK, mt * BM, 1, pr.a_b[sg], full0 + 8 * s);
+          tma_load_4d(base + 2 * A_BYTES, mb, kt * BK, nt * BN, 0, pr.b_b[sg], full0 + 8 * s);
+          tma_load_4d(base + 2 * A_BYTES + B_BYTES, mb, kt * BK, nt * BN, 1, pr.b_b[sg], full0 + 8 * s);
         }
       }
       if (!ok) {
@@ -251,12 +308,11 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcPa
   } else if (warp == 1) {
     if (lane == 0) {
       // ---------------- MMA issuer ----------------
-      int it = 0, i = 0, p = 0;
+      int it = 0, i = 0, t, kb, ke, KT;
       bool ok = true, issued = false;
-      for (int t = blockIdx.x; ok && t < P.total_tiles; t += G, ++i) {
-        p = find_prob(P.probs, P.n_prob, t, p);
-        const TcProb& pr = P.probs[p];
-        const int ktot = P.nseg * (2 * pr.Np) / BK;
+      UnitCursor cur;
+      cursor_init(P, cur);
+      while (ok && cursor_next(P, cur, t, kb, ke, KT)) {
         const int ab = i & 1, u = i >> 1;
         if (!mbar_wait(acce0 + 8 * ab, (u & 1) ^ 1, P.timeout_ns, abort_flag, P.err)) {
           ok = false;
@@ -264,7 +320,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcPa
         }
         tc_fence_after();
         const uint32_t d = tmem + ab * BN;
-        for (int kk = 0; kk < ktot; ++kk, ++it) {
+        for (int kk = kb; kk < ke; ++kk, ++it) {
           const int s = it % ST, r = it / ST;
           if (!mbar_wait(full0 + 8 * s, r & 1, P.timeout_ns, abort_flag, P.err)) {
             ok = false;
@@ -278,7 +334,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcPa
             const uint64_t al = sw128_desc(base + A_BYTES + 32 * j);
             const uint64_t bh = sw128_desc(base + 2 * A_BYTES + 32 * j);
             const uint64_t bl = sw128_desc(base + 2 * A_BYTES + B_BYTES + 32 * j);
-            tc_mma(d, ah, bh, IDESC, (kk | j) != 0);
+            tc_mma(d, ah, bh, IDESC, (kk > kb || j > 0) ? 1u : 0u);
             tc_mma(d, ah, bl, IDESC, 1u);
             tc_mma(d, al, bh, IDESC, 1u);
           }
@@ -287,6 +343,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcPa
         }
         if (!ok) break;
         tc_commit(accf0 + 8 * ab);
+        ++i;
       }
       if (!ok && issued) {
         tc_commit(drain);
@@ -295,28 +352,88 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcPa
     }
   } else {
     // ---------------- epilogue (warps 2..5 -> TMEM lane quarters 2,3,0,1) ----------------
+    // Thread 64 takes every wait of the group and publishes the outcome in
+    // shared memory before a group barrier, so the four warps always agree.
     const int q = warp & 3;
-    int i = 0, p = 0;
-    for (int t = blockIdx.x; t < P.total_tiles; t += G, ++i) {
-      p = find_prob(P.probs, P.n_prob, t, p);
-      const TcProb& pr = P.probs[p];
+    const bool leader = threadIdx.x == 64;
+    int i = 0, t, kb, ke, KT;
+    UnitCursor cur;
+    cursor_init(P, cur);
+    while (cursor_next(P, cur, t, kb, ke, KT)) {
+      const TcProb& pr = P.probs[cur.p];
       const int local = t - pr.tile0;
       const int mt = local % pr.tiles_m, nt = local / pr.tiles_m;
       const int ab = i & 1, u = i >> 1;
-      int ok = 1;
-      if (lane == 0) ok = mbar_wait(accf0 + 8 * ab, u & 1, P.timeout_ns, abort_flag, P.err) ? 1 : 0;
-      ok = __shfl_sync(0xffffffffu, ok, 0);
-      if (!ok) break;
+      const bool contrib = P.streamk && kb > 0;
+      const bool finish = P.streamk && kb == 0 && ke < KT;
+      int c_last = blockIdx.x;
+      if (finish) {
+        // CTAs after this one hold the rest of the tile's k-iterations
+        const long long x = (long long)pr.iter0 + (long long)local * KT + KT - 1;
+        c_last = blockIdx.x + 1;
+        while (c_last + 1 < (int)gridDim.x && sk_start(P, c_last + 1) <= x) ++c_last;
+      }
+      if (leader) {
+        int ok = mbar_wait(accf0 + 8 * ab, u & 1, P.timeout_ns, abort_flag, P.err) ? 1 : 0;
+        for (int c2 = blockIdx.x + 1; ok && finish && c2 <= c_last; ++c2) {
+          // bounded wait for the partial of CTA c2
+          long long t0 = 0;
+          for (int spin = 0;; ++spin) {
+            if (*reinterpret_cast<volatile int*>(P.flags + c2)) break;
+            if ((spin & 31) == 31) {
+              if (*abort_flag) {
+                ok = 0;
+                break;
+              }
+              const long long now = gtime();
+              if (t0 == 0) {
+                t0 = now;
+              } else if (now - t0 > P.timeout_ns) {
+                *abort_flag = 1;
+                atomicOr(P.err, 2);
+                ok = 0;
+                break;
+              }
+            }
+          }
+        }
+        __threadfence();
+        s_epi_ok[i & 1] = ok;
+      }
+      epi_bar();
+      if (!s_epi_ok[i & 1]) break;
       tc_fence_after();
       const int Np = pr.Np;
       const long long ld = 2LL * Np;
-      const int row = mt * BM + q * 32 + lane;
+      const int rt = q * 32 + lane;  // row within the tile
+      const int row = mt * BM + rt;
 #pragma unroll 1
       for (int c0 = 0; c0 < BN; c0 += 32) {
         uint32_t r[32];
         const uint32_t taddr = tmem + ab * BN + c0 + ((uint32_t)(q * 32) << 16);
         TMEM_LD32(taddr, r);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (contrib) {
+          float4* w = reinterpret_cast<float4*>(P.ws + ((size_t)blockIdx.x * BM + rt) * BN + c0);
+#pragma unroll
+          for (int v = 0; v < 8; ++v)
+            w[v] = make_float4(__uint_as_float(r[4 * v]), __uint_as_float(r[4 * v + 1]), __uint_as_float(r[4 * v + 2]),
+                               __uint_as_float(r[4 * v + 3]));
+          continue;
+        }
+        if (finish) {
+          for (int c2 = blockIdx.x + 1; c2 <= c_last; ++c2) {
+            const float4* w = reinterpret_cast<const float4*>(P.ws + ((size_t)c2 * BM + rt) * BN + c0);
+#pragma unroll
+            for (int v = 0; v < 8; ++v) {
+              const float4 f = __ldcg(w + v);
+              r[4 * v] = __float_as_uint(__uint_as_float(r[4 * v]) + f.x);
+              r[4 * v + 1] = __float_as_uint(__uint_as_float(r[4 * v + 1]) + f.y);
+              r[4 * v + 2] = __float_as_uint(__uint_as_float(r[4 * v + 2]) + f.z);
+              r[4 * v + 3] = __float_as_uint(__uint_as_float(r[4 * v + 3]) + f.w);
+            }
+          }
+        }
         const int gn = nt * BN + c0;
         if (EPI == 1) {
           float* X = reinterpret_cast<float*>(pr.out) + row * ld + gn;
@@ -357,6 +474,18 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcPa
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(acce0 + 8 * ab);
+      if (contrib) {
+        // publish the partial: every writer fences, then one flag store
+        __threadfence();
+        epi_bar();
+        if (leader) atomicExch(P.flags + blockIdx.x, 1);
+      } else if (finish) {
+        // every thread has read the partials: release the slots
+        epi_bar();
+        if (leader)
+          for (int c2 = blockIdx.x + 1; c2 <= c_last; ++c2) atomicExch(P.flags + c2, 0);
+      }
+      ++i;
     }
   }
   tc_fence_before();

@@ -73,3 +73,21 @@ def test_split_timeout_returns_error_and_context_recovers():
     with gpu_run(name, 20, precision=vgtb.SPLIT_BF16X3) as ok:
         J, _, _ = ok.observables(0)
     assert np.all(np.isfinite(J))
+
+
+def test_split_rerun_bitwise_and_autotuned_variants_agree():
+    """The stream-K fixup sums partials in a fixed order: reruns are bitwise equal.
+    The autotuner's choice (stream-K or classic tiles, 128 or 256 wide) stays within
+    the product tolerance of the default."""
+    from paper_2308_09782_gb300 import vgtb
+    name, nsteps = "si64_pulse", 200
+    with gpu_run(name, nsteps, precision=vgtb.SPLIT_BF16X3) as a, \
+            gpu_run(name, nsteps, precision=vgtb.SPLIT_BF16X3) as b, \
+            gpu_run(name, nsteps, precision=vgtb.SPLIT_BF16X3, autotune=1) as c:
+        Ja, _, _ = a.observables(0)
+        Jb, _, _ = b.observables(0)
+        Jc, _, _ = c.observables(0)
+        assert np.array_equal(Ja, Jb)
+        assert np.array_equal(a.get_density(0, 5), b.get_density(0, 5))
+    ref = oracle_run(name, nsteps)
+    assert rel_fro([Jc], [ref["J"]]) <= 1e-4
