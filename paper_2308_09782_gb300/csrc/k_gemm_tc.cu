@@ -51,11 +51,12 @@ bool encode_map(CUtensorMap* m, const void* base, int cols, int rows, int batch,
 }
 
 struct Variant {
-  int bn, st, streamk;
+  int bn, st, streamk, pair;
 };
-// tile width, pipeline stages, stream-K schedule (autotune candidates; the first is the default)
-constexpr Variant kVariants[] = {{256, 2, 0}, {256, 2, 1}, {128, 3, 0}, {128, 3, 1}};
-constexpr int kNumVariants = 4;
+// tile width (per CTA, or per pair for the 2-SM variant), pipeline stages,
+// stream-K schedule, 2-SM pair (autotune candidates)
+constexpr Variant kVariants[] = {{256, 3, 0, 1}, {256, 2, 0, 0}, {256, 2, 1, 0}, {128, 3, 0, 0}, {128, 3, 1, 0}};
+constexpr int kNumVariants = 5;
 
 template <int BN, int ST, int EPI>
 int smem_bytes() {
@@ -68,6 +69,28 @@ cudaError_t launch_t(const TcPlan* p, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+template <int ST, int EPI>
+int smem_pair() {
+  return ST * (2 * BM * BK * 2 + 2 * 128 * BK * 2) + 1024 + 256;
+}
+
+template <int ST, int EPI>
+cudaError_t launch_pair(const TcPlan* p, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(p->grid, 1, 1);
+  cfg.blockDim = dim3(192, 1, 1);
+  cfg.dynamicSmemBytes = p->smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_tc_gemm2<ST, EPI>, p->P);
+}
+
 template <int BN, int ST, int EPI>
 cudaError_t configure_t() {
   return cudaFuncSetAttribute(k_tc_gemm<BN, ST, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -75,19 +98,27 @@ cudaError_t configure_t() {
 }
 
 cudaError_t launch_variant(const TcPlan* p, cudaStream_t st) {
+  if (kVariants[p->variant].pair) return p->epi == 0 ? launch_pair<3, 0>(p, st) : launch_pair<3, 1>(p, st);
   const bool wide = kVariants[p->variant].bn == 256;
   if (p->epi == 0) return wide ? launch_t<256, 2, 0>(p, st) : launch_t<128, 3, 0>(p, st);
   return wide ? launch_t<256, 2, 1>(p, st) : launch_t<128, 3, 1>(p, st);
 }
 
-int variant_smem(int v) { return kVariants[v].bn == 256 ? smem_bytes<256, 2, 0>() : smem_bytes<128, 3, 0>(); }
+int variant_smem(int v) {
+  if (kVariants[v].pair) return smem_pair<3, 0>();
+  return kVariants[v].bn == 256 ? smem_bytes<256, 2, 0>() : smem_bytes<128, 3, 0>();
+}
 
 cudaError_t configure_all() {
   cudaError_t e;
   if ((e = configure_t<256, 2, 0>()) != cudaSuccess) return e;
   if ((e = configure_t<128, 3, 0>()) != cudaSuccess) return e;
   if ((e = configure_t<256, 2, 1>()) != cudaSuccess) return e;
-  return configure_t<128, 3, 1>();
+  if ((e = configure_t<128, 3, 1>()) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_tc_gemm2<3, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_pair<3, 0>())) !=
+      cudaSuccess)
+    return e;
+  return cudaFuncSetAttribute(k_tc_gemm2<3, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_pair<3, 1>());
 }
 
 }  // namespace
@@ -103,6 +134,9 @@ int tc_gemm_supported() {
 static int build_one(const std::vector<TcSysView>& sys, const std::vector<DevItem>& items, int epi, int variant,
                      long long timeout_ns, TcPlan* plan, std::string* msg) {
   const int BNv = kVariants[variant].bn;
+  const bool pair = kVariants[variant].pair != 0;
+  const int bbox = pair ? BNv / 2 : BNv;  // B rows loaded by one CTA
+  const int tm_rows = pair ? 2 * BM : BM;  // output rows of one tile
   memset(&plan->P, 0, sizeof(plan->P));
   plan->epi = epi;
   plan->variant = variant;
@@ -116,11 +150,11 @@ static int build_one(const std::vector<TcSysView>& sys, const std::vector<DevIte
     if (epi == 0) {
       if (!encode_map(&plan->P.mA[s][0], v.dD_p, 2 * Np, Np, v.n_items, BM, msg)) return -1;
       if (!encode_map(&plan->P.mA[s][1], v.D0_p, 2 * Np, Np, v.nk, BM, msg)) return -1;
-      if (!encode_map(&plan->P.mB[s][0], v.Hemb_p, 2 * Np, 2 * Np, v.n_items, BNv, msg)) return -1;
-      if (!encode_map(&plan->P.mB[s][1], v.dHemb_p, 2 * Np, 2 * Np, v.n_items, BNv, msg)) return -1;
+      if (!encode_map(&plan->P.mB[s][0], v.Hemb_p, 2 * Np, 2 * Np, v.n_items, bbox, msg)) return -1;
+      if (!encode_map(&plan->P.mB[s][1], v.dHemb_p, 2 * Np, 2 * Np, v.n_items, bbox, msg)) return -1;
     } else {
       if (!encode_map(&plan->P.mA[s][0], v.Sinv_p, 2 * Np, Np, v.nk, BM, msg)) return -1;
-      if (!encode_map(&plan->P.mB[s][0], v.Wemb_p, 2 * Np, 2 * Np, v.n_items, BNv, msg)) return -1;
+      if (!encode_map(&plan->P.mB[s][0], v.Wemb_p, 2 * Np, 2 * Np, v.n_items, bbox, msg)) return -1;
     }
   }
   std::vector<TcProb> probs;
@@ -133,7 +167,7 @@ static int build_one(const std::vector<TcSysView>& sys, const std::vector<DevIte
     pr.sys = it.sys;
     const int li = local[it.sys]++;
     pr.Np = v.Np;
-    pr.tiles_m = v.Np / BM;
+    pr.tiles_m = v.Np / tm_rows;
     pr.tiles_n = 2 * v.Np / BNv;
     pr.tile0 = tiles;
     if (epi == 0) {
@@ -171,6 +205,7 @@ static int build_one(const std::vector<TcSysView>& sys, const std::vector<DevIte
   plan->P.timeout_ns = timeout_ns;
   plan->grid = std::min(tiles, nsm);
   plan->smem = variant_smem(variant);
+  if (pair) plan->grid = 2 * std::min(tiles, nsm / 2);
   // stream-K needs every CTA to own at least one k-iteration; otherwise fall back
   if (kVariants[variant].streamk && iters >= 2LL * nsm) {
     plan->grid = nsm;
@@ -214,15 +249,18 @@ int tc_build_plans(const std::vector<TcSysView>& sys, const std::vector<DevItem>
   for (int epi = 0; epi < 2; ++epi) {
     TcPlan* best = nullptr;
     double best_ms = 1e30;
-    const int nv = autotune ? kNumVariants : 1;
-    for (int v = 0; v < nv; ++v) {
+    bool pair_ok = true;
+    for (const TcSysView& s : sys) pair_ok &= (s.Np % (2 * BM) == 0);
+    const int first = pair_ok ? 0 : 1;
+    const int nv = autotune ? kNumVariants : first + 1;
+    for (int v = first; v < nv; ++v) {
       TcPlan* p = new TcPlan();
       if (build_one(sys, items, epi, v, timeout_ns, p, msg)) {
         tc_destroy_plan(p);
         tc_destroy_plan(best);
         return -1;
       }
-      if (nv > 1) {
+      if (nv - first > 1) {
         const double ms = time_plan(p, st);
         int err = 0;
         cudaMemcpy(&err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost);

@@ -496,4 +496,269 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcPa
   }
 }
 
+// ----------------------------------------------------------------------------
+// 2-SM pair variant: a cluster of two CTAs computes a 256 x 256 tile with
+// tcgen05.mma.cta_group::2 (M = 256: each CTA holds 128 rows of A and of the
+// accumulator; N = 256: each CTA holds half of the B tile).  Per SM this moves
+// a third less operand data through shared memory and L2 per flop than the
+// 128 x 256 single-CTA tile.  The pair's loads all complete on the leader's
+// (rank 0) full barrier; the leader's single MMA thread issues every MMA and
+// its commits arrive on both CTAs' barriers; both CTAs' epilogue warps arrive
+// on the leader's accumulator-empty barrier.  Classic tile loop over pair
+// tiles; problem tiles are counted in 256 x 256 units.
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+__device__ __forceinline__ uint32_t map_to_rank0(uint32_t saddr) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(0));
+  return r;
+}
+
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tma_load_4d_pair(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                                 uint32_t bar_cluster) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.cta_group::2.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
+      "%3, %4, %5}], [%6];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar_cluster)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_mma_pair(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_commit_pair(uint32_t bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
+      "h"(mask)
+      : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar_cluster) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar_cluster) : "memory");
+}
+
+template <int ST, int EPI>
+__global__ void __launch_bounds__(192, 1) k_tc_gemm2(const __grid_constant__ TcParams P) {
+  constexpr int BNP = 256;                                  // pair tile width
+  constexpr uint32_t A_BYTES = BM * BK * 2;                 // this CTA's 128 rows of A, per piece
+  constexpr uint32_t B_BYTES = (BNP / 2) * BK * 2;          // this CTA's half of B, per piece
+  constexpr uint32_t STAGE = 2 * A_BYTES + 2 * B_BYTES;
+  constexpr uint32_t TCOLS = 2 * BNP;
+  constexpr uint32_t IDESC = idesc_bf16(2 * BM, BNP);
+  extern __shared__ uint8_t smraw[];
+  uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + ST * STAGE);
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + ST), accf0 = smem_u32(bars + 2 * ST),
+                 acce0 = smem_u32(bars + 2 * ST + 2), drain = smem_u32(bars + 2 * ST + 4);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * ST + 5);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);  // [0] abort, [1..2] epilogue ok
+  volatile int* s_epi_ok = abort_flag + 1;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_rank();
+  const bool leader_cta = rank == 0;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < ST; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    mbar_init(accf0, 1);
+    mbar_init(accf0 + 8, 1);
+    mbar_init(acce0, 8);
+    mbar_init(acce0 + 8, 8);
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TCOLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync_all();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t full_l = map_to_rank0(full0), acce_l = map_to_rank0(acce0);
+  const int pair = blockIdx.x >> 1, G2 = gridDim.x >> 1;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer (both CTAs) ----------------
+      int it = 0, p = 0;
+      bool ok = true;
+      for (int t = pair; ok && t < P.total_tiles; t += G2) {
+        p = find_prob(P.probs, P.n_prob, t, p);
+        const TcProb& pr = P.probs[p];
+        const int local = t - pr.tile0;
+        const int mt = local % pr.tiles_m, nt = local / pr.tiles_m;
+        const int kts = (2 * pr.Np) / BK;
+        const int arow = mt * (2 * BM) + rank * BM, brow = nt * BNP + rank * (BNP / 2);
+        for (int kk = 0; kk < P.nseg * kts; ++kk, ++it) {
+          const int sg = kk / kts, kt = kk - sg * kts;
+          const CUtensorMap* ma = &P.mA[pr.sys][sg];
+          const CUtensorMap* mb = &P.mB[pr.sys][sg];
+          const int s = it % ST, r = it / ST;
+          if (!mbar_wait(empty0 + 8 * s, (r & 1) ^ 1, P.timeout_ns, abort_flag, P.err)) {
+            ok = false;
+            break;
+          }
+          const uint32_t base = smem_u32(sm + s * STAGE);
+          if (leader_cta) mbar_expect_tx(full0 + 8 * s, 2 * STAGE);
+          const uint32_t fb = full_l + 8 * s;
+          tma_load_4d_pair(base, ma, kt * BK, arow, 0, pr.a_b[sg], fb);
+          tma_load_4d_pair(base + A_BYTES, ma, kt * BK, arow, 1, pr.a_b[sg], fb);
+          tma_load_4d_pair(base + 2 * A_BYTES, mb, kt * BK, brow, 0, pr.b_b[sg], fb);
+          tma_load_4d_pair(base + 2 * A_BYTES + B_BYTES, mb, kt * BK, brow, 1, pr.b_b[sg], fb);
+        }
+      }
+      if (!ok) {
+        if (leader_cta) {
+          // the leader's full barriers also count the peer's bytes of the same iterations
+          for (int j = (it > ST ? it - ST : 0); j < it; ++j)
+            mbar_wait(full0 + 8 * (j % ST), (j / ST) & 1, kDrainNs, abort_flag, P.err, false);
+        } else {
+          // the peer cannot wait on the leader's barriers: give its copies time to land
+          const long long t0 = gtime();
+          while (gtime() - t0 < 200000) {
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0 && leader_cta) {
+      // ---------------- MMA issuer (leader CTA only) ----------------
+      int it = 0, i = 0, p = 0;
+      bool ok = true, issued = false;
+      for (int t = pair; ok && t < P.total_tiles; t += G2, ++i) {
+        p = find_prob(P.probs, P.n_prob, t, p);
+        const TcProb& pr = P.probs[p];
+        const int ktot = P.nseg * (2 * pr.Np) / BK;
+        const int ab = i & 1, u = i >> 1;
+        if (!mbar_wait(acce0 + 8 * ab, (u & 1) ^ 1, P.timeout_ns, abort_flag, P.err)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d = tmem + ab * BNP;
+        for (int kk = 0; kk < ktot; ++kk, ++it) {
+          const int s = it % ST, r = it / ST;
+          if (!mbar_wait(full0 + 8 * s, r & 1, P.timeout_ns, abort_flag, P.err)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t base = smem_u32(sm + s * STAGE);
+#pragma unroll
+          for (int j = 0; j < BK / 16; ++j) {
+            const uint64_t ah = sw128_desc(base + 32 * j);
+            const uint64_t al = sw128_desc(base + A_BYTES + 32 * j);
+            const uint64_t bh = sw128_desc(base + 2 * A_BYTES + 32 * j);
+            const uint64_t bl = sw128_desc(base + 2 * A_BYTES + B_BYTES + 32 * j);
+            tc_mma_pair(d, ah, bh, IDESC, (kk | j) != 0);
+            tc_mma_pair(d, ah, bl, IDESC, 1u);
+            tc_mma_pair(d, al, bh, IDESC, 1u);
+          }
+          tc_commit_pair(empty0 + 8 * s, 3);
+          issued = true;
+        }
+        if (!ok) break;
+        tc_commit_pair(accf0 + 8 * ab, 3);
+      }
+      if (!ok && issued) {
+        tc_commit_pair(drain, 1);
+        mbar_wait(drain, 0, kDrainNs, abort_flag, P.err, false);
+      }
+    }
+  } else {
+    // ---------------- epilogue (warps 2..5 of both CTAs) ----------------
+    const int q = warp & 3;
+    const bool leader = threadIdx.x == 64;
+    int i = 0, p = 0;
+    for (int t = pair; t < P.total_tiles; t += G2, ++i) {
+      p = find_prob(P.probs, P.n_prob, t, p);
+      const TcProb& pr = P.probs[p];
+      const int local = t - pr.tile0;
+      const int mt = local % pr.tiles_m, nt = local / pr.tiles_m;
+      const int ab = i & 1, u = i >> 1;
+      if (leader) {
+        s_epi_ok[i & 1] = mbar_wait(accf0 + 8 * ab, u & 1, P.timeout_ns, abort_flag, P.err) ? 1 : 0;
+      }
+      epi_bar();
+      if (!s_epi_ok[i & 1]) break;
+      tc_fence_after();
+      const int Np = pr.Np;
+      const long long ld = 2LL * Np;
+      const int row = mt * (2 * BM) + rank * BM + q * 32 + lane;
+#pragma unroll 1
+      for (int c0 = 0; c0 < BNP; c0 += 32) {
+        uint32_t r[32];
+        const uint32_t taddr = tmem + ab * BNP + c0 + ((uint32_t)(q * 32) << 16);
+        TMEM_LD32(taddr, r);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        const int gn = nt * BNP + c0;
+        if (EPI == 1) {
+          float* X = reinterpret_cast<float*>(pr.out) + row * ld + gn;
+#pragma unroll
+          for (int v = 0; v < 8; ++v)
+            reinterpret_cast<float4*>(X)[v] =
+                make_float4(__uint_as_float(r[4 * v]), __uint_as_float(r[4 * v + 1]), __uint_as_float(r[4 * v + 2]),
+                            __uint_as_float(r[4 * v + 3]));
+        } else {
+          __nv_bfloat16* W = reinterpret_cast<__nv_bfloat16*>(pr.out);
+          const long long P1 = 4LL * Np * Np;
+          const bool imag = gn >= Np;
+          const long long top = row * ld + gn;
+          const long long bot = (long long)(Np + row) * ld + (imag ? gn - Np : gn + Np);
+          const float sgn = imag ? -1.f : 1.f;
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            uint32_t hi[4], lo[4], nhi[4], nlo[4];
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+              const float a = __uint_as_float(r[8 * v + 2 * w]), b = __uint_as_float(r[8 * v + 2 * w + 1]);
+              const __nv_bfloat16 ah = __float2bfloat16_rn(a), bh = __float2bfloat16_rn(b);
+              const float al = a - __bfloat162float(ah), bl = b - __bfloat162float(bh);
+              hi[w] = pack_bf16(__bfloat162float(ah), __bfloat162float(bh));
+              lo[w] = pack_bf16(al, bl);
+              nhi[w] = pack_bf16(sgn * __bfloat162float(ah), sgn * __bfloat162float(bh));
+              nlo[w] = pack_bf16(sgn * al, sgn * bl);
+            }
+            reinterpret_cast<uint4*>(W + top)[v] = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+            reinterpret_cast<uint4*>(W + P1 + top)[v] = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+            reinterpret_cast<uint4*>(W + bot)[v] = make_uint4(nhi[0], nhi[1], nhi[2], nhi[3]);
+            reinterpret_cast<uint4*>(W + P1 + bot)[v] = make_uint4(nlo[0], nlo[1], nlo[2], nlo[3]);
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive_cluster(acce_l + 8 * ab);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync_all();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS) : "memory");
+  }
+}
+
 }  // namespace vgtb

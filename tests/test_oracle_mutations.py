@@ -2,7 +2,8 @@
 
 Each case monkeypatches one oracle function with a plausible error (sign of
 Eq. 6, the 1/2 of Eq. 10, the sign of Eq. 14, a transposed momentum block,
-a missing |A|^2 term in the energy or a missing diamagnetic current) and checks that the pin aimed at it fails.  Everything
+a missing |A|^2 term in the energy, a missing diamagnetic current, the sign of
+the A.P term) and checks that the pin aimed at it fails.  Everything
 here runs on the CPU.
 """
 import numpy as np
@@ -31,6 +32,13 @@ def _no_half_h2(H0, S, P, A, eps_orb):
     A = np.asarray(A, float)
     H = H0 + (eps_orb[:, None] * S + S * eps_orb[None, :])
     H = H + (A[0] * P[0] + A[1] * P[1] + A[2] * P[2]) / C
+    return H + (A @ A) / (2.0 * C ** 2) * S
+
+
+def _minus_ap(H0, S, P, A, eps_orb):
+    A = np.asarray(A, float)
+    H = H0 + 0.5 * (eps_orb[:, None] * S + S * eps_orb[None, :])
+    H = H - (A[0] * P[0] + A[1] * P[1] + A[2] * P[2]) / C
     return H + (A @ A) / (2.0 * C ** 2) * S
 
 
@@ -74,6 +82,7 @@ def _transposed_p(sysd, kred):
     ("current", _plus_current, "p8"),
     ("current", _current_no_diamagnetic, "p8"),
     ("bloch_matrices", _transposed_p, "p14"),
+    ("hamiltonian", _minus_ap, "p13"),
 ])
 def test_pin_catches_planted_mistake(monkeypatch, target, mutant, pin):
     monkeypatch.setattr(ov, target, mutant)
@@ -86,3 +95,5 @@ def test_pin_catches_planted_mistake(monkeypatch, target, mutant, pin):
             pins.test_p4_a_squared_term_is_a_pure_phase(_si8())
         elif pin == "p8":
             pins.test_p8_work_theorem_second_order(_si8())
+        elif pin == "p13":
+            pins.test_p13_constant_a_is_a_gauge_transformation_to_first_order()

@@ -302,3 +302,46 @@ def test_ground_state_properties(si8):
     for D, S in zip(gs["D"], ctx["S"]):
         assert abs(np.trace(D @ S).real - s["n_electrons"]) < 1e-11
         np.testing.assert_allclose(D @ S @ D, 2 * D, atol=1e-11)
+
+
+def test_p13_constant_a_is_a_gauge_transformation_to_first_order():
+    """P-13: orthonormal ring with P = i[H0, X]: H(A) = U H0 U^dagger + O(A^2) with
+    U = exp(-i A.X / c), so D' = U D0 U^dagger is stationary under a constant A up to
+    O(A^2); a wrong sign of the (1/c) A.P term of Eq. 12 would make it drift at O(A)."""
+    nat = 6
+    rng = np.random.default_rng(13)
+    ang = 2 * np.pi * np.arange(nat) / nat
+    pos = np.stack([5.0 * np.cos(ang), 5.0 * np.sin(ang), np.zeros(nat)], 1) + rng.normal(0, 0.1, (nat, 3))
+    H0 = np.zeros((nat, nat))
+    for i in range(nat):
+        H0[i, i] = -0.3 + 0.05 * rng.normal()
+        j = (i + 1) % nat
+        H0[i, j] = H0[j, i] = -0.1 * (1 + 0.1 * rng.normal())
+    ijl, h0, s, ds = [], [], [], []
+    for i in range(nat):
+        for j in range(nat):
+            if i == j or H0[i, j] != 0.0:
+                ijl.append((i, j, 0, 0, 0))
+                h0.append(H0[i, j])
+                s.append(1.0 if i == j else 0.0)
+                # dS/dR_J such that P = i dS = i [H0, X]:  [H0, X]_ij = H0_ij (x_j - x_i)
+                ds.append(H0[i, j] * (pos[j] - pos[i]))
+    sysd = {"lattice": np.eye(3) * 1000.0, "pos": pos, "orb_offset": np.arange(nat + 1, dtype=np.int32),
+            "z_ref": np.ones(nat), "blk_ijl": np.array(ijl, np.int32), "h0": np.array(h0), "s": np.array(s),
+            "ds": np.array(ds).T.copy(), "gamma": np.zeros((nat, nat)), "kpt": np.zeros((1, 3)),
+            "wk": np.ones(1), "n_electrons": float(nat), "dt": 0.1}
+    ctx = O.setup(sysd)
+    gs = O.ground_state(sysd, ctx=ctx)
+    n = 400
+    devs = []
+    for a0 in (4.0, 2.0):
+        A = np.tile([a0, 0.5 * a0, 0.0], (n + 1, 1))
+        U = np.diag(np.exp(-1j * (pos @ A[0]) / O.C_LIGHT))
+        Dg = U @ gs["D"][0] @ U.conj().T
+        r = O.propagate(sysd, A, n, [Dg], ctx=ctx)
+        devs.append(np.linalg.norm(r["D"][0] - Dg))
+        # a first-order (wrong-sign) error would show up as drift of size O(A)
+        Dw = U.conj().T @ gs["D"][0] @ U
+        rw = O.propagate(sysd, A, n, [Dw], ctx=ctx)
+        assert np.linalg.norm(rw["D"][0] - Dw) > 5 * devs[-1]
+    assert 3.5 < devs[0] / devs[1] < 4.5
