@@ -314,7 +314,7 @@ def native(args):
                      "product2_achieved": round(ach2, 1), "product2_frac": round(ach2 / peak, 4)},
         "kernel_ms_per_step": {k: round(v, 4) for k, v in kern_ms.items()},
         "cpu_baseline": cpu, "e2e": e2e,
-        "gpu_launches": 6 * K + 2,
+        "gpu_launches": 7 * K + 3,
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)

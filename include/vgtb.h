@@ -148,6 +148,27 @@ int vgtb_get_density(vgtb_ctx* ctx, int traj, int k, double* d_out);
  * Errors: E_INVALID (index), E_STATE (no density yet). */
 int vgtb_get_initial_density(vgtb_ctx* ctx, int sys_index, int k, double* d_out);
 
+/* Conductivity and dielectric function from the current of a kick (Eqs. 15,
+ * 16) of trajectory `traj`, over its stored levels n0..n1 (0 <= n0 < n1 <=
+ * steps done):  sigma_i(w) = (1/e0) int_0^T e^{iwt} J_i(t) exp(-t/tau0) dt with
+ * t = (n - n0) dt (trapezoid rule), eps_i(w) = 1 + 4 pi i sigma_i(w) / w.
+ * e0 is the kick strength, E(t) = e0 delta(t) along the kick direction (a kick
+ * A(t) = A0 for t >= 0 has e0 = -A0/c, Eq. 3); tau0 = 200 a.u. in the paper.
+ * omega: [n_omega] host array of frequencies > 0.  sigma, eps: caller-owned
+ * host arrays [n_omega][3] complex (interleaved doubles), component i = x,y,z.
+ * Errors: E_INVALID, E_STATE (levels not yet propagated). */
+int vgtb_spectrum(vgtb_ctx* ctx, int traj, int n0, int n1, double e0, double tau0, int n_omega,
+                  const double* omega, double* sigma, double* eps);
+
+/* Charge transfer between atom groups (the per-class Mulliken analysis of
+ * Sec. 3.3): dQ_g(t_n) = sum_{I in g} (Q_I(t_n) - Q_I(t_0)) with atomic charge
+ * Q_I = -(q_I - Z_I), for every stored charge level (every obs_stride steps up
+ * to the current step).  group: [n_atoms] host array, group index of each atom
+ * in 0..n_groups-1 or negative for none.  out: caller-owned host array
+ * [n_levels][n_groups], n_levels = steps_done / obs_stride + 1.
+ * Errors: E_INVALID, E_STATE (no field set). */
+int vgtb_group_charges(vgtb_ctx* ctx, int traj, int n_groups, const int* group, double* out);
+
 /* Checkpoint: the state is D_k(t_n), D_k(t_{n-1}) of every trajectory and k,
  * plus n.  vgtb_state_size() gives the byte size of the host buffer. */
 long long vgtb_state_size(const vgtb_ctx* ctx);

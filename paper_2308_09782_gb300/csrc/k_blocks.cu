@@ -1,6 +1,7 @@
 // Block-sparse kernels of one propagation step:
 //   k_obs         - Mulliken, current and energy partial sums from D_k(t_n) (Eqs. 10, 14)
-//   k_scc         - dq, eps = gamma dq, J, E per trajectory (Eq. 10, Eq. 14)
+//   k_scc_atoms,
+//   k_scc_eps     - dq, eps = gamma dq, J, E per trajectory (Eq. 10, Eq. 14)
 //   k_phase       - Bloch sum of H_k(t_n) with the vector potential (Eqs. 7-12), FP64
 //   k_phase_split - the same sum in FP32, written as embedded BF16 hi/lo pieces
 // A half-warp (16 lanes) handles one target (I, J) of one trajectory: it walks the
@@ -146,14 +147,17 @@ void launch_obs(const DevSys* sys, const DevTraj* trj, const DevItem* items, con
 }
 
 // ---------------------------------------------------------------------------
-// k_scc: kSccRows rows of eps per CTA, nblk CTAs per trajectory.
-// Every CTA rebuilds dq (cheap sums of the per-target partials) in shared
-// memory; CTA 0 also finishes J, the band energy, the charge record and the
-// checks; each CTA writes eps_I and dq_I eps_I for its rows; the last CTA to
-// arrive adds dq.eps/2 to the band energy in a fixed order.
+// SCC reduction in two launches per step (all trajectories at once):
+//   k_scc_atoms: one warp per atom sums the partials of the atom's targets
+//                (targets are sorted by row atom): q_I, dq_I, and the atom's
+//                share of T_a and of the band energy;
+//   k_scc_eps:   kSccRows rows of eps = gamma dq per CTA (Eq. 10); the last CTA
+//                of a trajectory adds up J (Eq. 14), the band energy and
+//                dq.eps/2 in a fixed order and runs the checks.
 // ---------------------------------------------------------------------------
 constexpr int kSccThreads = 256;
 constexpr int kSccRows = 32;
+constexpr int kAtomsPerCta = kSccThreads / 32;
 
 template <int NT>
 __device__ void block_sum5(double (&v)[5], double* sh) {
@@ -173,9 +177,38 @@ __device__ void block_sum5(double (&v)[5], double* sh) {
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(kSccThreads) k_scc(const DevSys* __restrict__ sysv, DevTraj* trj, int n_traj,
-                                                    int nblk, const int* __restrict__ step, int stride,
-                                                    int fixed_step, int record) {
+__global__ void __launch_bounds__(kSccThreads) k_scc_atoms(const DevSys* __restrict__ sysv, DevTraj* trj, int n_traj,
+                                                          int nblk, const int* __restrict__ step, int stride,
+                                                          int fixed_step, int record) {
+  const int t = blockIdx.x / nblk, b = blockIdx.x % nblk;
+  if (t >= n_traj) return;
+  DevTraj& T = trj[t];
+  const DevSys& S = sysv[T.sys];
+  const int I = b * kAtomsPerCta + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (I >= S.nat) return;
+  const int n = fixed_step >= 0 ? fixed_step : *step;
+  double v[5] = {0, 0, 0, 0, 0};
+  for (int tg = S.atom_tgt0[I] + lane; tg < S.atom_tgt0[I + 1]; tg += 32) {
+    const double* p = T.part + 5LL * tg;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) v[i] += p[i];
+  }
+#pragma unroll
+  for (int i = 0; i < 5; ++i) v[i] = warp_sum(v[i]);
+  if (lane == 0) {
+    T.dq[I] = v[0] - S.z[I];
+    if (record && T.q && n % stride == 0) T.q[(long long)(n / stride) * S.nat + I] = v[0];
+    double* a = T.apart + 4LL * I;
+    a[0] = v[1];
+    a[1] = v[2];
+    a[2] = v[3];
+    a[3] = v[4];
+  }
+}
+
+__global__ void __launch_bounds__(kSccThreads) k_scc_eps(const DevSys* __restrict__ sysv, DevTraj* trj, int n_traj,
+                                                        int nblk, const int* __restrict__ step, int fixed_step,
+                                                        int record) {
   extern __shared__ double sm[];  // [kSccThreads*5] reduction + [nat] dq
   __shared__ int s_last;
   const int t = blockIdx.x / nblk, b = blockIdx.x % nblk;
@@ -188,20 +221,8 @@ __global__ void __launch_bounds__(kSccThreads) k_scc(const DevSys* __restrict__ 
   double* red = sm;
   double* dq = sm + 5 * kSccThreads;
   const int tid = threadIdx.x;
-  const bool rec_q = record && T.q && (n % stride == 0) && b == 0;
-  double acc[5] = {0, 0, 0, 0, 0};  // sum q, Tx, Ty, Tz, Eband
-  for (int I = tid; I < S.nat; I += kSccThreads) {
-    double q = 0.0;
-    for (int tg = S.atom_tgt0[I]; tg < S.atom_tgt0[I + 1]; ++tg) q += T.part[5LL * tg];
-    dq[I] = q - S.z[I];
-    acc[0] += q;
-    if (b == 0) {
-      T.dq[I] = dq[I];
-      if (rec_q) T.q[(long long)(n / stride) * S.nat + I] = q;
-    }
-  }
+  for (int I = tid; I < S.nat; I += kSccThreads) dq[I] = T.dq[I];
   __syncthreads();
-  // eps rows of this CTA: one warp per row, lanes over K
   const int warp = tid >> 5, lane = tid & 31;
   const int r0 = b * kSccRows, r1 = min(S.nat, r0 + kSccRows);
   for (int I = r0 + warp; I < r1; I += kSccThreads / 32) {
@@ -214,29 +235,7 @@ __global__ void __launch_bounds__(kSccThreads) k_scc(const DevSys* __restrict__ 
       T.erow[I] = dq[I] * e;
     }
   }
-  if (b == 0) {
-    for (int tg = tid; tg < S.n_tgt; tg += kSccThreads) {
-      acc[1] += T.part[5LL * tg + 1];
-      acc[2] += T.part[5LL * tg + 2];
-      acc[3] += T.part[5LL * tg + 3];
-      acc[4] += T.part[5LL * tg + 4];
-    }
-    block_sum5<kSccThreads>(acc, red);
-    if (tid == 0) {
-      const double J0 = -acc[1] / S.omega, J1 = -acc[2] / S.omega, J2 = -acc[3] / S.omega;
-      if (record) {
-        T.J[3LL * n] = J0;
-        T.J[3LL * n + 1] = J1;
-        T.J[3LL * n + 2] = J2;
-      }
-      *T.eband = acc[4];
-      int st = 0;
-      if (!isfinite(J0) || !isfinite(J1) || !isfinite(J2) || !isfinite(acc[0])) st |= ST_NONFINITE;
-      if (fabs(acc[0] - S.nel) > 1e-6 * fmax(1.0, S.nel)) st |= ST_DRIFT;
-      if (st) atomicOr(T.status, st);
-    }
-  }
-  // last CTA of this trajectory: E = E_band + dq.eps / 2 in a fixed order
+  // last CTA of this trajectory: J, E and the checks in a fixed order
   __syncthreads();
   if (tid == 0) {
     __threadfence();
@@ -245,13 +244,33 @@ __global__ void __launch_bounds__(kSccThreads) k_scc(const DevSys* __restrict__ 
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  double v[5] = {0, 0, 0, 0, 0};
-  for (int I = tid; I < S.nat; I += kSccThreads) v[0] += T.erow[I];
+  double v[5] = {0, 0, 0, 0, 0};  // Tx, Ty, Tz, E_band, dq.eps
+  double qsum = 0.0;
+  for (int I = tid; I < S.nat; I += kSccThreads) {
+    const double* a = T.apart + 4LL * I;
+    v[0] += a[0];
+    v[1] += a[1];
+    v[2] += a[2];
+    v[3] += a[3];
+    v[4] += T.erow[I];
+    qsum += dq[I] + S.z[I];
+  }
   block_sum5<kSccThreads>(v, red);
+  double w[5] = {qsum, 0, 0, 0, 0};
+  block_sum5<kSccThreads>(w, red);
   if (tid == 0) {
-    const double E = *T.eband + 0.5 * v[0];
-    if (record) T.E[n] = E;
-    if (!isfinite(E)) atomicOr(T.status, ST_NONFINITE);
+    const double J0 = -v[0] / S.omega, J1 = -v[1] / S.omega, J2 = -v[2] / S.omega;
+    const double E = v[3] + 0.5 * v[4];
+    if (record) {
+      T.J[3LL * n] = J0;
+      T.J[3LL * n + 1] = J1;
+      T.J[3LL * n + 2] = J2;
+      T.E[n] = E;
+    }
+    int st = 0;
+    if (!isfinite(J0) || !isfinite(J1) || !isfinite(J2) || !isfinite(E) || !isfinite(w[0])) st |= ST_NONFINITE;
+    if (fabs(w[0] - S.nel) > 1e-6 * fmax(1.0, S.nel)) st |= ST_DRIFT;
+    if (st) atomicOr(T.status, st);
     *T.ticket = 0;
   }
 }
@@ -259,16 +278,19 @@ __global__ void __launch_bounds__(kSccThreads) k_scc(const DevSys* __restrict__ 
 int scc_configure(int max_nat) {
   const size_t sm = sizeof(double) * (5 * kSccThreads + (size_t)max_nat);
   if (sm > 48 * 1024) {
-    if (cudaFuncSetAttribute(k_scc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(k_scc_eps, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
+      return -1;
   }
   return 0;
 }
 
 void launch_scc(const DevSys* sys, DevTraj* trj, int n_traj, const int* step, int stride, int fixed_step,
                 int record, int max_nat, cudaStream_t st) {
+  const int nblk_a = (max_nat + kAtomsPerCta - 1) / kAtomsPerCta;
+  k_scc_atoms<<<n_traj * nblk_a, kSccThreads, 0, st>>>(sys, trj, n_traj, nblk_a, step, stride, fixed_step, record);
   const int nblk = (max_nat + kSccRows - 1) / kSccRows;
   const size_t sm = sizeof(double) * (5 * kSccThreads + (size_t)max_nat);
-  k_scc<<<n_traj * nblk, kSccThreads, sm, st>>>(sys, trj, n_traj, nblk, step, stride, fixed_step, record);
+  k_scc_eps<<<n_traj * nblk, kSccThreads, sm, st>>>(sys, trj, n_traj, nblk, step, fixed_step, record);
 }
 
 // ---------------------------------------------------------------------------

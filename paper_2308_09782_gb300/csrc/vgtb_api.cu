@@ -66,7 +66,7 @@ struct HostTraj {
   double* eps = nullptr;
   double* part = nullptr;
   double* erow = nullptr;
-  double* eband = nullptr;
+  double* apart = nullptr;
   int* ticket = nullptr;
   int* status = nullptr;
 };
@@ -699,7 +699,7 @@ int upload_traj_table(vgtb_ctx* ctx) {
     d.eps = h.eps;
     d.part = h.part;
     d.erow = h.erow;
-    d.eband = h.eband;
+    d.apart = h.apart;
     d.ticket = h.ticket;
     d.status = h.status;
   }
@@ -954,7 +954,7 @@ int vgtb_create_batch(vgtb_ctx** out, int n_sys, const vgtb_system* sys, int n_t
     if ((rc = dalloc(ctx, &T.eps, h.nat))) return bail(rc);
     if ((rc = dalloc(ctx, &T.part, 5 * (size_t)h.n_tgt))) return bail(rc);
     if ((rc = dalloc(ctx, &T.erow, h.nat))) return bail(rc);
-    if ((rc = dalloc(ctx, &T.eband, 1))) return bail(rc);
+    if ((rc = dalloc(ctx, &T.apart, 4 * (size_t)h.nat))) return bail(rc);
     if ((rc = dalloc(ctx, &T.ticket, 1))) return bail(rc);
     if ((rc = dalloc(ctx, &T.status, 1))) return bail(rc);
   }
@@ -1172,6 +1172,58 @@ int vgtb_get_density(vgtb_ctx* ctx, int t, int k, double* d_out) {
       d_out[2 * ((size_t)i * h.N + j)] = v.x;
       d_out[2 * ((size_t)i * h.N + j) + 1] = v.y;
     }
+  return VGTB_OK;
+}
+
+int vgtb_spectrum(vgtb_ctx* ctx, int t, int n0, int n1, double e0, double tau0, int n_omega, const double* omega,
+                  double* sigma, double* eps) {
+  if (!ctx) return VGTB_E_INVALID;
+  if (t < 0 || t >= (int)ctx->trj.size()) return fail(ctx, VGTB_E_INVALID, "trajectory %d out of range", t);
+  const HostTraj& T = ctx->trj[t];
+  if (!T.J) return fail(ctx, VGTB_E_STATE, "no field set for trajectory %d", t);
+  if (n0 < 0 || n1 <= n0) return fail(ctx, VGTB_E_INVALID, "need 0 <= n0 < n1");
+  if (n1 > ctx->n_done) return fail(ctx, VGTB_E_STATE, "level %d not propagated yet (%d steps done)", n1, ctx->n_done);
+  if (n_omega < 1 || !omega || !sigma || !eps) return fail(ctx, VGTB_E_INVALID, "empty frequency list or NULL output");
+  if (!(e0 != 0.0) || !std::isfinite(e0) || !(tau0 > 0.0)) return fail(ctx, VGTB_E_INVALID, "need e0 != 0, tau0 > 0");
+  for (int i = 0; i < n_omega; ++i)
+    if (!(omega[i] > 0.0) || !std::isfinite(omega[i])) return fail(ctx, VGTB_E_INVALID, "frequencies must be > 0");
+  double *dw = nullptr, *ds = nullptr, *de = nullptr;
+  CK(cudaMallocAsync(&dw, sizeof(double) * n_omega, ctx->stream));
+  CK(cudaMallocAsync(&ds, sizeof(double) * 6 * n_omega, ctx->stream));
+  CK(cudaMallocAsync(&de, sizeof(double) * 6 * n_omega, ctx->stream));
+  CK(cudaMemcpyAsync(dw, omega, sizeof(double) * n_omega, cudaMemcpyHostToDevice, ctx->stream));
+  launch_conductivity(T.J, n0, n1, ctx->sys[T.sys].dt, e0, tau0, dw, n_omega, ds, de, ctx->stream);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(sigma, ds, sizeof(double) * 6 * n_omega, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(eps, de, sizeof(double) * 6 * n_omega, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaFreeAsync(dw, ctx->stream));
+  CK(cudaFreeAsync(ds, ctx->stream));
+  CK(cudaFreeAsync(de, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return VGTB_OK;
+}
+
+int vgtb_group_charges(vgtb_ctx* ctx, int t, int n_groups, const int* group, double* out) {
+  if (!ctx) return VGTB_E_INVALID;
+  if (t < 0 || t >= (int)ctx->trj.size()) return fail(ctx, VGTB_E_INVALID, "trajectory %d out of range", t);
+  const HostTraj& T = ctx->trj[t];
+  if (!T.q) return fail(ctx, VGTB_E_STATE, "no field set for trajectory %d", t);
+  const int nat = ctx->sys[T.sys].nat;
+  if (n_groups < 1 || !group || !out) return fail(ctx, VGTB_E_INVALID, "need n_groups >= 1 and non-NULL arrays");
+  for (int i = 0; i < nat; ++i)
+    if (group[i] >= n_groups) return fail(ctx, VGTB_E_INVALID, "group[%d] = %d >= n_groups", i, group[i]);
+  const int nlev = ctx->n_done / ctx->opt.obs_stride + 1;
+  int* dg = nullptr;
+  double* dout = nullptr;
+  CK(cudaMallocAsync(&dg, sizeof(int) * nat, ctx->stream));
+  CK(cudaMallocAsync(&dout, sizeof(double) * (size_t)nlev * n_groups, ctx->stream));
+  CK(cudaMemcpyAsync(dg, group, sizeof(int) * nat, cudaMemcpyHostToDevice, ctx->stream));
+  launch_group_charge(T.q, nat, dg, n_groups, nlev, dout, ctx->stream);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(out, dout, sizeof(double) * (size_t)nlev * n_groups, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaFreeAsync(dg, ctx->stream));
+  CK(cudaFreeAsync(dout, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
   return VGTB_OK;
 }
 

@@ -75,7 +75,7 @@ struct DevTraj {
   double* eps;             // [nat] current eps
   double* part;            // [n_tgt][5] per-target partial sums
   double* erow;            // [nat] dq_I eps_I (energy of the SCC term, per row)
-  double* eband;           // [1] band energy of the current level
+  double* apart;           // [nat][4] per-atom shares of T_x, T_y, T_z and the band energy
   int* ticket;             // [1] CTA arrival counter of k_scc (reset by the last CTA)
   int* status;
 };
@@ -151,6 +151,12 @@ void launch_split_planar(const double2* src, __nv_bfloat16* dst, int N, int Np, 
 void launch_increment(int* step, cudaStream_t st);
 void launch_hermitize(double2* a, int n, int ld, cudaStream_t st);
 void launch_split_embedded(const double2* src, __nv_bfloat16* dst, int Np, cudaStream_t st);
+
+// post-propagation reductions (k_spectrum.cu)
+void launch_conductivity(const double* J, int n0, int n1, double dt, double e0, double tau0, const double* omega,
+                         int n_omega, double* sigma, double* eps, cudaStream_t st);
+void launch_group_charge(const double* q, int nat, const int* group, int n_groups, int n_levels, double* out,
+                         cudaStream_t st);
 
 // tcgen05 split-precision complex GEMM (k_gemm_tc.cu)
 struct TcGemmPlan;   // opaque, built on the host

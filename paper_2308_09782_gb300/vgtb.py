@@ -29,7 +29,7 @@ EXPORTS = ["vgtb_default_options", "vgtb_create", "vgtb_create_batch", "vgtb_set
            "vgtb_set_field", "vgtb_propagate", "vgtb_steps_done", "vgtb_observables",
            "vgtb_get_density", "vgtb_get_initial_density", "vgtb_state_size", "vgtb_get_state", "vgtb_set_state",
            "vgtb_profile", "vgtb_kernel_stats", "vgtb_last_error", "vgtb_destroy",
-           "vgtb_diag_split_chain", "vgtb_split_cgemm_noalloc"]
+           "vgtb_diag_split_chain", "vgtb_split_cgemm_noalloc", "vgtb_spectrum", "vgtb_group_charges"]
 
 
 class VgtbSystem(C.Structure):
@@ -86,6 +86,8 @@ def load(path: str = LIB_PATH):
     lib.vgtb_destroy.restype = None
     lib.vgtb_diag_split_chain.argtypes = [I, P(D), P(D), P(D), P(D), P(D)]
     lib.vgtb_split_cgemm_noalloc.argtypes = [I, V, V, V, V]
+    lib.vgtb_spectrum.argtypes = [ctxp, I, I, I, D, D, I, P(D), P(D), P(D)]
+    lib.vgtb_group_charges.argtypes = [ctxp, I, I, P(I), P(D)]
     for name in EXPORTS:
         if name not in ("vgtb_default_options", "vgtb_last_error", "vgtb_destroy", "vgtb_state_size"):
             getattr(lib, name).restype = I
@@ -225,6 +227,25 @@ class Context:
         """Copy the series into caller arrays (e.g. pinned host memory)."""
         self._check(load().vgtb_observables(self._h, traj, _dptr(J), _dptr(E),
                                             _dptr(q) if q is not None else None))
+
+    def spectrum(self, traj: int, e0: float, omegas, n0: int = 0, n1: int | None = None, tau0: float = 200.0):
+        """sigma(w), eps(w) [n_omega, 3] complex of Eqs. 15-16 from the device J series."""
+        w = np.ascontiguousarray(omegas, np.float64)
+        n1 = self.steps_done if n1 is None else n1
+        sig = np.zeros((len(w), 3), np.complex128)
+        eps = np.zeros((len(w), 3), np.complex128)
+        cp = lambda m: m.ctypes.data_as(C.POINTER(C.c_double))  # noqa: E731
+        self._check(load().vgtb_spectrum(self._h, traj, n0, n1, float(e0), float(tau0), len(w), _dptr(w),
+                                         cp(sig), cp(eps)))
+        return sig, eps
+
+    def group_charges(self, traj: int, group, n_groups: int):
+        """dQ_g(t_n) = sum_{I in g} (Q_I(t_n) - Q_I(t_0)), Q_I = -(q_I - Z_I), [n_levels, n_groups]."""
+        g = np.ascontiguousarray(group, np.int32)
+        nlev = self.steps_done // self._opt.obs_stride + 1
+        out = np.zeros((nlev, n_groups))
+        self._check(load().vgtb_group_charges(self._h, traj, n_groups, _iptr(g), _dptr(out)))
+        return out
 
     def get_initial_density(self, sys_index: int, k: int):
         out = np.zeros((self.N[sys_index], self.N[sys_index]), np.complex128)
