@@ -53,13 +53,14 @@ __device__ __forceinline__ Unit unit_of(const int* wpre, int n_traj, int total) 
 }
 
 // ---------------------------------------------------------------------------
-// Partial sums per target, summed over k with weights w_k:
-//   q   : sum Re(D_{mu nu} conj(S_k,mu nu))                 (Eq. 10: [D S]_{mu mu})
-//   T_a : sum Re(D_{mu nu} conj(Pi^a_k,mu nu))              (Eq. 14: Tr[D Pi^a])
-//   E   : sum Re(D_{mu nu} conj((H0 + (A/c).P + |A|^2/2c^2 S)_{mu nu}))
-// With u = D e^{+i k.L} (conjugated phase) an image contributes
-//   q += s Re u,  T_a += ds_a Im u + (A_a/c) s Re u,
-//   E += (h0 + alpha s) Re u + ((A/c).ds) Im u,   because P = i dS/dR_J.
+// Partial sums per target, summed over k with weights w_k, from the
+// time-independent k-space blocks S_k, P_k^a, H0_k (Bloch-summed at setup):
+//   s_S = sum Re(D conj(S_k)),  s_a = sum Re(D conj(P^a_k)),  s_H = sum Re(D conj(H0_k))
+//   q = s_S                                          (Eq. 10: [D S]_{mu mu})
+//   T_a = s_a + (A_a/c) s_S                          (Eq. 14: Tr[D Pi^a], Pi = P + (A/c) S)
+//   E_band = s_H + (A/c).(s_x, s_y, s_z) + |A|^2/(2c^2) s_S
+// In the delta forms D = D0 + dD and the D0 part of every sum is a constant
+// computed once (obs0), so only dD is read.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_obs(const DevSys* __restrict__ sysv, const DevTraj* __restrict__ trj,
                                              const DevItem* __restrict__ items, const int* __restrict__ wpre,
@@ -67,76 +68,152 @@ __global__ void __launch_bounds__(256) k_obs(const DevSys* __restrict__ sysv, co
                                              int fixed_step) {
   const Unit U = unit_of(wpre, n_traj, total);
   const int lane = threadIdx.x & 15;
-  double aq = 0.0, ax = 0.0, ay = 0.0, az = 0.0, ae = 0.0;
+  double sS = 0.0, sx = 0.0, sy = 0.0, sz = 0.0, sH = 0.0;
   const DevTraj& T = trj[U.t];
   const DevSys& S = sysv[T.sys];
+  int n = 0;
   if (U.active) {
-    const int n = fixed_step >= 0 ? fixed_step : *step;
+    n = fixed_step >= 0 ? fixed_step : *step;
     const int par = n & 1;
+    const int I = S.tgt_I[U.tg], J = S.tgt_J[U.tg];
+    const int oi = S.orb_off[I];
+    const int oj = S.orb_off[J], nj = S.orb_off[J + 1] - oj;
+    const int el0 = S.tgt_el0[U.tg], nel = S.tgt_el0[U.tg + 1] - el0;
+    for (int k = 0; k < S.nk; ++k) {
+      const double2* Dk = items[T.item0 + k].D[par];
+      const long long kb = (long long)k * S.n_el + el0;
+      const long long pstride = (long long)S.nk * S.n_el;
+      double lS = 0.0, lx = 0.0, ly = 0.0, lz = 0.0, lH = 0.0;
+      for (int e = lane; e < nel; e += 16) {
+        const int a = e / nj, b = e - a * nj;
+        const double2 d = Dk[(long long)(oi + a) * S.Np + (oj + b)];
+        const double2 cs = S.kS[kb + e], ch = S.kH0[kb + e];
+        const double2 px = S.kP[kb + e], py = S.kP[pstride + kb + e], pz = S.kP[2 * pstride + kb + e];
+        lS += d.x * cs.x + d.y * cs.y;
+        lx += d.x * px.x + d.y * px.y;
+        ly += d.x * py.x + d.y * py.y;
+        lz += d.x * pz.x + d.y * pz.y;
+        lH += d.x * ch.x + d.y * ch.y;
+      }
+      const double wk = S.wk[k];
+      sS += wk * lS;
+      sx += wk * lx;
+      sy += wk * ly;
+      sz += wk * lz;
+      sH += wk * lH;
+    }
+  }
+  sS = half_sum(sS);
+  sx = half_sum(sx);
+  sy = half_sum(sy);
+  sz = half_sum(sz);
+  sH = half_sum(sH);
+  if (U.active && lane == 0) {
+    if (delta) {
+      const double* o = S.obs0 + 5LL * U.tg;
+      sS += o[0];
+      sx += o[1];
+      sy += o[2];
+      sz += o[3];
+      sH += o[4];
+    }
     double A0 = 0.0, A1 = 0.0, A2 = 0.0;
     if (T.A) {
       A0 = T.A[3 * n];
       A1 = T.A[3 * n + 1];
       A2 = T.A[3 * n + 2];
     }
-    const double ic = 1.0 / kLight;
-    const double alpha = (A0 * A0 + A1 * A1 + A2 * A2) * 0.5 * ic * ic;
+    constexpr double ic = 1.0 / kLight;
     const double a0 = A0 * ic, a1 = A1 * ic, a2 = A2 * ic;
-    const int I = S.tgt_I[U.tg], J = S.tgt_J[U.tg];
-    const int oi = S.orb_off[I], ni = S.orb_off[I + 1] - oi;
+    const double alpha = 0.5 * (a0 * a0 + a1 * a1 + a2 * a2);
+    double* p = T.part + 5LL * U.tg;
+    p[0] = sS;
+    p[1] = sx + a0 * sS;
+    p[2] = sy + a1 * sS;
+    p[3] = sz + a2 * sS;
+    p[4] = sH + (a0 * sx + a1 * sy + a2 * sz) + alpha * sS;
+  }
+}
+
+// Setup: the k-space blocks of one system at one k (half-warp per target).
+__global__ void k_kblocks(const DevSys* __restrict__ sysv, int s_idx, int k) {
+  const int tg = (blockIdx.x * blockDim.x + threadIdx.x) >> 4;
+  const int lane = threadIdx.x & 15;
+  const DevSys& S = sysv[s_idx];
+  if (tg >= S.n_tgt) return;
+  const int el0 = S.tgt_el0[tg], nel = S.tgt_el0[tg + 1] - el0;
+  const long long kb = (long long)k * S.n_el + el0, pstride = (long long)S.nk * S.n_el;
+  for (int e = lane; e < nel; e += 16) {
+    double2 s = make_double2(0.0, 0.0), h = s, px = s, py = s, pz = s;
+    for (int g = S.tgt_img0[tg]; g < S.tgt_img0[tg + 1]; ++g) {
+      const long long off = S.img_off[g] + e;
+      const double2 ph = S.phase[(long long)k * S.n_blk + S.img_blk[g]];
+      const double sv = S.s[off], hv = S.h0[off];
+      s.x += ph.x * sv;
+      s.y += ph.y * sv;
+      h.x += ph.x * hv;
+      h.y += ph.y * hv;
+      // ph * (i ds):  (-ph.y ds, ph.x ds)
+      const double dx = S.ds[off], dy = S.ds[S.ds_stride + off], dz = S.ds[2 * S.ds_stride + off];
+      px.x -= ph.y * dx;
+      px.y += ph.x * dx;
+      py.x -= ph.y * dy;
+      py.y += ph.x * dy;
+      pz.x -= ph.y * dz;
+      pz.y += ph.x * dz;
+    }
+    S.kS[kb + e] = s;
+    S.kH0[kb + e] = h;
+    S.kP[kb + e] = px;
+    S.kP[pstride + kb + e] = py;
+    S.kP[2 * pstride + kb + e] = pz;
+  }
+}
+
+void launch_kblocks(const DevSys* sys, int s_idx, int n_tgt, int k, cudaStream_t st) {
+  const int threads = 256;
+  const int blocks = (n_tgt * 16 + threads - 1) / threads;
+  k_kblocks<<<blocks, threads, 0, st>>>(sys, s_idx, k);
+}
+
+// Setup (delta forms): obs0[tg] = the k_obs sums of the target evaluated with D0.
+__global__ void k_obs0(const DevSys* __restrict__ sysv, int s_idx) {
+  const int tg = (blockIdx.x * blockDim.x + threadIdx.x) >> 4;
+  const int lane = threadIdx.x & 15;
+  const DevSys& S = sysv[s_idx];
+  const bool active = tg < S.n_tgt;
+  double v[5] = {0, 0, 0, 0, 0};
+  if (active) {
+    const int I = S.tgt_I[tg], J = S.tgt_J[tg];
+    const int oi = S.orb_off[I];
     const int oj = S.orb_off[J], nj = S.orb_off[J + 1] - oj;
-    const int nel = ni * nj;
-    const int g0 = S.tgt_img0[U.tg], g1 = S.tgt_img0[U.tg + 1];
-    const long long NN = (long long)S.Np * S.Np;
+    const int el0 = S.tgt_el0[tg], nel = S.tgt_el0[tg + 1] - el0;
+    const long long NN = (long long)S.Np * S.Np, pstride = (long long)S.nk * S.n_el;
     for (int k = 0; k < S.nk; ++k) {
-      const double2* Dk = items[T.item0 + k].D[par];
-      const double2* D0k = S.D0 + k * NN;
-      const double wk = S.wk[k];
+      const long long kb = (long long)k * S.n_el + el0;
+      double l[5] = {0, 0, 0, 0, 0};
       for (int e = lane; e < nel; e += 16) {
         const int a = e / nj, b = e - a * nj;
-        const long long idx = (long long)(oi + a) * S.Np + (oj + b);
-        double2 d = Dk[idx];
-        if (delta) {
-          const double2 d0 = D0k[idx];
-          d.x += d0.x;
-          d.y += d0.y;
-        }
-        double lq = 0.0, lx = 0.0, ly = 0.0, lz = 0.0, le = 0.0;
-        for (int g = g0; g < g1; ++g) {
-          const long long off = S.img_off[g] + e;
-          const double sv = S.s[off], hv = S.h0[off];
-          const double dx = S.ds[off], dy = S.ds[S.ds_stride + off], dz = S.ds[2 * S.ds_stride + off];
-          const double2 ph = S.phase[(long long)k * S.n_blk + S.img_blk[g]];
-          const double ur = d.x * ph.x + d.y * ph.y;
-          const double ui = d.y * ph.x - d.x * ph.y;
-          const double sur = sv * ur;
-          lq += sur;
-          lx += dx * ui + a0 * sur;
-          ly += dy * ui + a1 * sur;
-          lz += dz * ui + a2 * sur;
-          le += (hv + alpha * sv) * ur + (a0 * dx + a1 * dy + a2 * dz) * ui;
-        }
-        aq += wk * lq;
-        ax += wk * lx;
-        ay += wk * ly;
-        az += wk * lz;
-        ae += wk * le;
+        const double2 d = S.D0[k * NN + (long long)(oi + a) * S.Np + (oj + b)];
+        const double2 c[5] = {S.kS[kb + e], S.kP[kb + e], S.kP[pstride + kb + e], S.kP[2 * pstride + kb + e],
+                              S.kH0[kb + e]};
+#pragma unroll
+        for (int i = 0; i < 5; ++i) l[i] += d.x * c[i].x + d.y * c[i].y;
       }
+#pragma unroll
+      for (int i = 0; i < 5; ++i) v[i] += S.wk[k] * l[i];
     }
   }
-  aq = half_sum(aq);
-  ax = half_sum(ax);
-  ay = half_sum(ay);
-  az = half_sum(az);
-  ae = half_sum(ae);
-  if (U.active && lane == 0) {
-    double* p = T.part + 5LL * U.tg;
-    p[0] = aq;
-    p[1] = ax;
-    p[2] = ay;
-    p[3] = az;
-    p[4] = ae;
-  }
+#pragma unroll
+  for (int i = 0; i < 5; ++i) v[i] = half_sum(v[i]);
+  if (active && lane == 0)
+    for (int i = 0; i < 5; ++i) S.obs0[5LL * tg + i] = v[i];
+}
+
+void launch_obs0(const DevSys* sys, int s_idx, int n_tgt, cudaStream_t st) {
+  const int threads = 256;
+  const int blocks = (n_tgt * 16 + threads - 1) / threads;
+  k_obs0<<<blocks, threads, 0, st>>>(sys, s_idx);
 }
 
 void launch_obs(const DevSys* sys, const DevTraj* trj, const DevItem* items, const int* warp_prefix,
@@ -151,12 +228,12 @@ void launch_obs(const DevSys* sys, const DevTraj* trj, const DevItem* items, con
 //   k_scc_atoms: one warp per atom sums the partials of the atom's targets
 //                (targets are sorted by row atom): q_I, dq_I, and the atom's
 //                share of T_a and of the band energy;
-//   k_scc_eps:   kSccRows rows of eps = gamma dq per CTA (Eq. 10); the last CTA
+//   k_scc_eps:   kSccRows rows of eps = gamma dq per CTA, one per warp (Eq. 10); the last CTA
 //                of a trajectory adds up J (Eq. 14), the band energy and
 //                dq.eps/2 in a fixed order and runs the checks.
 // ---------------------------------------------------------------------------
 constexpr int kSccThreads = 256;
-constexpr int kSccRows = 32;
+constexpr int kSccRows = 8;
 constexpr int kAtomsPerCta = kSccThreads / 32;
 
 template <int NT>
@@ -393,10 +470,11 @@ __global__ void __launch_bounds__(256) k_phase_split(const DevSys* __restrict__ 
   const DevSys& S = sysv[T.sys];
   const int n = *step;
   float a0 = 0.f, a1 = 0.f, a2 = 0.f;
-  if (T.A) {
-    a0 = (float)(T.A[3 * n] / kLight);
-    a1 = (float)(T.A[3 * n + 1] / kLight);
-    a2 = (float)(T.A[3 * n + 2] / kLight);
+  if (T.A) {  // multiply by the compile-time reciprocal: an FP64 division is a long sequence on GB300
+    constexpr double inv_c = 1.0 / kLight;
+    a0 = (float)(T.A[3 * n] * inv_c);
+    a1 = (float)(T.A[3 * n + 1] * inv_c);
+    a2 = (float)(T.A[3 * n + 2] * inv_c);
   }
   const int I = S.tgt_I[U.tg], J = S.tgt_J[U.tg];
   const int oi = S.orb_off[I], ni = S.orb_off[I + 1] - oi;

@@ -196,6 +196,38 @@ void launch_leap(const LeapItem* items, int n_items, int Np_max, int x_f32, cons
 }
 
 // ---------------------------------------------------------------------------
+// IEEE-754 float <-> double conversions done with integer bit operations.
+// GB300 runs FP64 instructions, conversions included, at a small fraction of
+// the integer rate, so the split leapfrog keeps only its two FP64 FMAs on the
+// FP64 pipe.  float -> double is exact (signed zero for float zeros and
+// subnormals, which are below 1.2e-38); double -> float rounds to nearest even
+// and flushes magnitudes below 2^-126 to signed zero and above the float range
+// to infinity.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double f2d_bits(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t e = (u >> 23) & 0xffu;
+  const uint32_t sign = u & 0x80000000u;
+  const uint32_t ee = (e == 255u) ? 2047u : e + 896u;  // exponent bias 1023 - 127
+  const uint32_t hi = (e == 0u) ? sign : (sign | (ee << 20) | ((u >> 3) & 0xfffffu));
+  const uint32_t lo = (e == 0u) ? 0u : (u << 29);
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+__device__ __forceinline__ float d2f_bits(double d) {
+  const uint32_t hi = (uint32_t)__double2hiint(d), lo = (uint32_t)__double2loint(d);
+  const uint32_t sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
+  const uint32_t mant = ((hi & 0xfffffu) << 3) | (lo >> 29);
+  const uint32_t rest = lo & 0x1fffffffu;
+  uint32_t f = sign | ((uint32_t)e << 23) | mant;
+  f += (rest > 0x10000000u || (rest == 0x10000000u && (mant & 1u))) ? 1u : 0u;
+  f = (e <= 0) ? sign : f;
+  f = (e >= 255) ? (sign | 0x7f800000u) : f;
+  return __uint_as_float(f);
+}
+
+// ---------------------------------------------------------------------------
 // Leapfrog of the split form: X (FP32 planar) and R0 (FP32 planar) give
 // dD/dt in FP32 with the same mirror-exact operations as k_leap; only the
 // master update dD_{n+1} = dD_{n-1} + 2 dt dD/dt is FP64 (GB300's FP64 rate is
@@ -252,9 +284,9 @@ __global__ void __launch_bounds__(256) k_leap_split(const LeapItem* __restrict__
           di = it.R0f[pr + Np] + di;
         }
         const double2 b = base[idx];
-        const double2 v = make_double2(fma(coef, (double)dr, b.x), fma(coef, (double)di, b.y));
+        const double2 v = make_double2(fma(coef, f2d_bits(dr), b.x), fma(coef, f2d_bits(di), b.y));
         it.D[nxt][idx] = v;
-        const float fr = (float)v.x, fi = (float)v.y;
+        const float fr = d2f_bits(v.x), fi = d2f_bits(v.y);
         const __nv_bfloat16 rh = __float2bfloat16_rn(fr), ih = __float2bfloat16_rn(fi);
         it.pieces[pr] = rh;
         it.pieces[P + pr] = __float2bfloat16_rn(fr - __bfloat162float(rh));

@@ -55,8 +55,9 @@ struct Variant {
 };
 // tile width (per CTA, or per pair for the 2-SM variant), pipeline stages,
 // stream-K schedule, 2-SM pair (autotune candidates)
-constexpr Variant kVariants[] = {{256, 3, 0, 1}, {256, 2, 0, 0}, {256, 2, 1, 0}, {128, 3, 0, 0}, {128, 3, 1, 0}};
-constexpr int kNumVariants = 5;
+constexpr Variant kVariants[] = {{256, 3, 0, 1}, {256, 3, 1, 1}, {256, 2, 0, 0}, {256, 2, 1, 0}, {128, 3, 0, 0},
+                                 {128, 3, 1, 0}};
+constexpr int kNumVariants = 6;
 
 template <int BN, int ST, int EPI>
 int smem_bytes() {
@@ -167,7 +168,7 @@ static int build_one(const std::vector<TcSysView>& sys, const std::vector<DevIte
     pr.sys = it.sys;
     const int li = local[it.sys]++;
     pr.Np = v.Np;
-    pr.tiles_m = v.Np / tm_rows;
+    pr.tiles_m = (v.Np + tm_rows - 1) / tm_rows;
     pr.tiles_n = 2 * v.Np / BNv;
     pr.tile0 = tiles;
     if (epi == 0) {
@@ -208,7 +209,7 @@ static int build_one(const std::vector<TcSysView>& sys, const std::vector<DevIte
   if (pair) plan->grid = 2 * std::min(tiles, nsm / 2);
   // stream-K needs every CTA to own at least one k-iteration; otherwise fall back
   if (kVariants[variant].streamk && iters >= 2LL * nsm) {
-    plan->grid = nsm;
+    plan->grid = pair ? (nsm & ~1) : nsm;  // pairs: workers are the nsm / 2 clusters
     plan->P.streamk = 1;
     plan->P.total_iters = iters;
     if (cudaMalloc(&plan->d_ws, sizeof(float) * (size_t)nsm * BM * BNv) != cudaSuccess ||
@@ -249,9 +250,7 @@ int tc_build_plans(const std::vector<TcSysView>& sys, const std::vector<DevItem>
   for (int epi = 0; epi < 2; ++epi) {
     TcPlan* best = nullptr;
     double best_ms = 1e30;
-    bool pair_ok = true;
-    for (const TcSysView& s : sys) pair_ok &= (s.Np % (2 * BM) == 0);
-    const int first = pair_ok ? 0 : 1;
+    const int first = 0;  // the pair kernel handles every Np (a multiple of 128)
     const int nv = autotune ? kNumVariants : first + 1;
     for (int v = first; v < nv; ++v) {
       TcPlan* p = new TcPlan();

@@ -187,19 +187,21 @@ struct UnitCursor {
   int t_next, p;
 };
 
-__device__ __forceinline__ long long sk_start(const TcParams& P, int c) {
-  return P.total_iters * (long long)c / (long long)gridDim.x;
+// first global k-iteration of worker c out of G (a worker is a CTA, or a CTA pair)
+__device__ __forceinline__ long long sk_start(const TcParams& P, int c, int G) {
+  return P.total_iters * (long long)c / (long long)G;
 }
 
-__device__ __forceinline__ void cursor_init(const TcParams& P, UnitCursor& u) {
+__device__ __forceinline__ void cursor_init(const TcParams& P, UnitCursor& u, int c, int G) {
   u.p = 0;
-  u.t_next = blockIdx.x;
-  u.it = P.streamk ? sk_start(P, blockIdx.x) : 0;
-  u.e = P.streamk ? sk_start(P, blockIdx.x + 1) : 0;
+  u.t_next = c;
+  u.it = P.streamk ? sk_start(P, c, G) : 0;
+  u.e = P.streamk ? sk_start(P, c + 1, G) : 0;
 }
 
 // next unit: global tile t, its k-iterations [kb, ke) out of KT; false when done
-__device__ __forceinline__ bool cursor_next(const TcParams& P, UnitCursor& u, int& t, int& kb, int& ke, int& KT) {
+__device__ __forceinline__ bool cursor_next(const TcParams& P, UnitCursor& u, int G, int& t, int& kb, int& ke,
+                                            int& KT) {
   if (P.streamk) {
     if (u.it >= u.e) return false;
     while (u.p + 1 < P.n_prob && P.probs[u.p + 1].iter0 <= u.it) ++u.p;
@@ -216,12 +218,39 @@ __device__ __forceinline__ bool cursor_next(const TcParams& P, UnitCursor& u, in
   }
   if (u.t_next >= P.total_tiles) return false;
   t = u.t_next;
-  u.t_next += gridDim.x;
+  u.t_next += G;
   u.p = find_prob(P.probs, P.n_prob, t, u.p);
   KT = P.nseg * (2 * P.probs[u.p].Np) / BK;
   kb = 0;
   ke = KT;
   return true;
+}
+
+// last worker that holds part of the tile whose k = 0 part ends worker c's range
+__device__ __forceinline__ int sk_last_worker(const TcParams& P, const TcProb& pr, int local, int KT, int c, int G) {
+  const long long x = (long long)pr.iter0 + (long long)local * KT + KT - 1;
+  int cl = c + 1;
+  while (cl + 1 < G && sk_start(P, cl + 1, G) <= x) ++cl;
+  return cl;
+}
+
+// bounded wait for a stream-K partial flag; false on timeout or abort
+__device__ __forceinline__ bool sk_wait_flag(const TcParams& P, int idx, volatile int* abort_flag) {
+  long long t0 = 0;
+  for (int spin = 0;; ++spin) {
+    if (*reinterpret_cast<volatile int*>(P.flags + idx)) return true;
+    if ((spin & 31) == 31) {
+      if (*abort_flag) return false;
+      const long long now = gtime();
+      if (t0 == 0) {
+        t0 = now;
+      } else if (now - t0 > P.timeout_ns) {
+        *abort_flag = 1;
+        atomicOr(P.err, 2);
+        return false;
+      }
+    }
+  }
 }
 
 __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
@@ -276,8 +305,8 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcPa
       int it = 0, t, kb, ke, KT;
       bool ok = true;
       UnitCursor cur;
-      cursor_init(P, cur);
-      while (ok && cursor_next(P, cur, t, kb, ke, KT)) {
+      cursor_init(P, cur, blockIdx.x, gridDim.x);
+      while (ok && cursor_next(P, cur, gridDim.x, t, kb, ke, KT)) {
         const TcProb& pr = P.probs[cur.p];
         const int local = t - pr.tile0;
         const int mt = local % pr.tiles_m, nt = local / pr.tiles_m;
@@ -311,8 +340,8 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcPa
       int it = 0, i = 0, t, kb, ke, KT;
       bool ok = true, issued = false;
       UnitCursor cur;
-      cursor_init(P, cur);
-      while (ok && cursor_next(P, cur, t, kb, ke, KT)) {
+      cursor_init(P, cur, blockIdx.x, gridDim.x);
+      while (ok && cursor_next(P, cur, gridDim.x, t, kb, ke, KT)) {
         const int ab = i & 1, u = i >> 1;
         if (!mbar_wait(acce0 + 8 * ab, (u & 1) ^ 1, P.timeout_ns, abort_flag, P.err)) {
           ok = false;
@@ -358,45 +387,19 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcPa
     const bool leader = threadIdx.x == 64;
     int i = 0, t, kb, ke, KT;
     UnitCursor cur;
-    cursor_init(P, cur);
-    while (cursor_next(P, cur, t, kb, ke, KT)) {
+    cursor_init(P, cur, blockIdx.x, gridDim.x);
+    while (cursor_next(P, cur, gridDim.x, t, kb, ke, KT)) {
       const TcProb& pr = P.probs[cur.p];
       const int local = t - pr.tile0;
       const int mt = local % pr.tiles_m, nt = local / pr.tiles_m;
       const int ab = i & 1, u = i >> 1;
       const bool contrib = P.streamk && kb > 0;
       const bool finish = P.streamk && kb == 0 && ke < KT;
-      int c_last = blockIdx.x;
-      if (finish) {
-        // CTAs after this one hold the rest of the tile's k-iterations
-        const long long x = (long long)pr.iter0 + (long long)local * KT + KT - 1;
-        c_last = blockIdx.x + 1;
-        while (c_last + 1 < (int)gridDim.x && sk_start(P, c_last + 1) <= x) ++c_last;
-      }
+      // CTAs after this one hold the rest of the tile's k-iterations
+      const int c_last = finish ? sk_last_worker(P, pr, local, KT, blockIdx.x, gridDim.x) : blockIdx.x;
       if (leader) {
         int ok = mbar_wait(accf0 + 8 * ab, u & 1, P.timeout_ns, abort_flag, P.err) ? 1 : 0;
-        for (int c2 = blockIdx.x + 1; ok && finish && c2 <= c_last; ++c2) {
-          // bounded wait for the partial of CTA c2
-          long long t0 = 0;
-          for (int spin = 0;; ++spin) {
-            if (*reinterpret_cast<volatile int*>(P.flags + c2)) break;
-            if ((spin & 31) == 31) {
-              if (*abort_flag) {
-                ok = 0;
-                break;
-              }
-              const long long now = gtime();
-              if (t0 == 0) {
-                t0 = now;
-              } else if (now - t0 > P.timeout_ns) {
-                *abort_flag = 1;
-                atomicOr(P.err, 2);
-                ok = 0;
-                break;
-              }
-            }
-          }
-        }
+        for (int c2 = blockIdx.x + 1; ok && finish && c2 <= c_last; ++c2) ok = sk_wait_flag(P, c2, abort_flag) ? 1 : 0;
         __threadfence();
         s_epi_ok[i & 1] = ok;
       }
@@ -499,7 +502,10 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcPa
 // ----------------------------------------------------------------------------
 // 2-SM pair variant: a cluster of two CTAs computes a 256 x 256 tile with
 // tcgen05.mma.cta_group::2 (M = 256: each CTA holds 128 rows of A and of the
-// accumulator; N = 256: each CTA holds half of the B tile).  Per SM this moves
+// accumulator; N = 256: each CTA holds half of the B tile).  Np is a multiple
+// of 128, so 2 Np is a multiple of 256 and only the last row tile can be half
+// outside the matrix: its A rows load as TMA zero fill and its stores are
+// skipped.  Per SM this moves
 // a third less operand data through shared memory and L2 per flop than the
 // 128 x 256 single-CTA tile.  The pair's loads all complete on the leader's
 // (rank 0) full barrier; the leader's single MMA thread issues every MMA and
@@ -601,16 +607,17 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm2(const __grid_constant__ TcP
   if (warp == 0) {
     if (lane == 0) {
       // ---------------- TMA producer (both CTAs) ----------------
-      int it = 0, p = 0;
+      int it = 0, t, kb, ke, KT;
       bool ok = true;
-      for (int t = pair; ok && t < P.total_tiles; t += G2) {
-        p = find_prob(P.probs, P.n_prob, t, p);
-        const TcProb& pr = P.probs[p];
+      UnitCursor cur;
+      cursor_init(P, cur, pair, G2);
+      while (ok && cursor_next(P, cur, G2, t, kb, ke, KT)) {
+        const TcProb& pr = P.probs[cur.p];
         const int local = t - pr.tile0;
         const int mt = local % pr.tiles_m, nt = local / pr.tiles_m;
         const int kts = (2 * pr.Np) / BK;
         const int arow = mt * (2 * BM) + rank * BM, brow = nt * BNP + rank * (BNP / 2);
-        for (int kk = 0; kk < P.nseg * kts; ++kk, ++it) {
+        for (int kk = kb; kk < ke; ++kk, ++it) {
           const int sg = kk / kts, kt = kk - sg * kts;
           const CUtensorMap* ma = &P.mA[pr.sys][sg];
           const CUtensorMap* mb = &P.mB[pr.sys][sg];
@@ -644,12 +651,11 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm2(const __grid_constant__ TcP
   } else if (warp == 1) {
     if (lane == 0 && leader_cta) {
       // ---------------- MMA issuer (leader CTA only) ----------------
-      int it = 0, i = 0, p = 0;
+      int it = 0, i = 0, t, kb, ke, KT;
       bool ok = true, issued = false;
-      for (int t = pair; ok && t < P.total_tiles; t += G2, ++i) {
-        p = find_prob(P.probs, P.n_prob, t, p);
-        const TcProb& pr = P.probs[p];
-        const int ktot = P.nseg * (2 * pr.Np) / BK;
+      UnitCursor cur;
+      cursor_init(P, cur, pair, G2);
+      for (; ok && cursor_next(P, cur, G2, t, kb, ke, KT); ++i) {
         const int ab = i & 1, u = i >> 1;
         if (!mbar_wait(acce0 + 8 * ab, (u & 1) ^ 1, P.timeout_ns, abort_flag, P.err)) {
           ok = false;
@@ -657,7 +663,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm2(const __grid_constant__ TcP
         }
         tc_fence_after();
         const uint32_t d = tmem + ab * BNP;
-        for (int kk = 0; kk < ktot; ++kk, ++it) {
+        for (int kk = kb; kk < ke; ++kk, ++it) {
           const int s = it % ST, r = it / ST;
           if (!mbar_wait(full0 + 8 * s, r & 1, P.timeout_ns, abort_flag, P.err)) {
             ok = false;
@@ -671,7 +677,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm2(const __grid_constant__ TcP
             const uint64_t al = sw128_desc(base + A_BYTES + 32 * j);
             const uint64_t bh = sw128_desc(base + 2 * A_BYTES + 32 * j);
             const uint64_t bl = sw128_desc(base + 2 * A_BYTES + B_BYTES + 32 * j);
-            tc_mma_pair(d, ah, bh, IDESC, (kk | j) != 0);
+            tc_mma_pair(d, ah, bh, IDESC, (kk > kb || j > 0) ? 1u : 0u);
             tc_mma_pair(d, ah, bl, IDESC, 1u);
             tc_mma_pair(d, al, bh, IDESC, 1u);
           }
@@ -688,31 +694,65 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm2(const __grid_constant__ TcP
     }
   } else {
     // ---------------- epilogue (warps 2..5 of both CTAs) ----------------
+    // stream-K: each CTA of a pair keeps its own 128 rows of a partial in the
+    // slot and flag of index 2 * pair + rank
     const int q = warp & 3;
     const bool leader = threadIdx.x == 64;
-    int i = 0, p = 0;
-    for (int t = pair; t < P.total_tiles; t += G2, ++i) {
-      p = find_prob(P.probs, P.n_prob, t, p);
-      const TcProb& pr = P.probs[p];
+    const int me = 2 * pair + (int)rank;
+    int i = 0, t, kb, ke, KT;
+    UnitCursor cur;
+    cursor_init(P, cur, pair, G2);
+    for (; cursor_next(P, cur, G2, t, kb, ke, KT); ++i) {
+      const TcProb& pr = P.probs[cur.p];
       const int local = t - pr.tile0;
       const int mt = local % pr.tiles_m, nt = local / pr.tiles_m;
       const int ab = i & 1, u = i >> 1;
+      const bool contrib = P.streamk && kb > 0;
+      const bool finish = P.streamk && kb == 0 && ke < KT;
+      const int p_last = finish ? sk_last_worker(P, pr, local, KT, pair, G2) : pair;
       if (leader) {
-        s_epi_ok[i & 1] = mbar_wait(accf0 + 8 * ab, u & 1, P.timeout_ns, abort_flag, P.err) ? 1 : 0;
+        int ok = mbar_wait(accf0 + 8 * ab, u & 1, P.timeout_ns, abort_flag, P.err) ? 1 : 0;
+        for (int p2 = pair + 1; ok && finish && p2 <= p_last; ++p2)
+          ok = sk_wait_flag(P, 2 * p2 + (int)rank, abort_flag) ? 1 : 0;
+        __threadfence();
+        s_epi_ok[i & 1] = ok;
       }
       epi_bar();
       if (!s_epi_ok[i & 1]) break;
       tc_fence_after();
       const int Np = pr.Np;
       const long long ld = 2LL * Np;
-      const int row = mt * (2 * BM) + rank * BM + q * 32 + lane;
+      const int rt = q * 32 + lane;
+      const int row = mt * (2 * BM) + rank * BM + rt;
 #pragma unroll 1
       for (int c0 = 0; c0 < BNP; c0 += 32) {
         uint32_t r[32];
         const uint32_t taddr = tmem + ab * BNP + c0 + ((uint32_t)(q * 32) << 16);
         TMEM_LD32(taddr, r);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (contrib) {
+          float4* w = reinterpret_cast<float4*>(P.ws + ((size_t)me * BM + rt) * BNP + c0);
+#pragma unroll
+          for (int v = 0; v < 8; ++v)
+            w[v] = make_float4(__uint_as_float(r[4 * v]), __uint_as_float(r[4 * v + 1]), __uint_as_float(r[4 * v + 2]),
+                               __uint_as_float(r[4 * v + 3]));
+          continue;
+        }
+        if (finish) {
+          for (int p2 = pair + 1; p2 <= p_last; ++p2) {
+            const float4* w = reinterpret_cast<const float4*>(P.ws + ((size_t)(2 * p2 + rank) * BM + rt) * BNP + c0);
+#pragma unroll
+            for (int v = 0; v < 8; ++v) {
+              const float4 f = __ldcg(w + v);
+              r[4 * v] = __float_as_uint(__uint_as_float(r[4 * v]) + f.x);
+              r[4 * v + 1] = __float_as_uint(__uint_as_float(r[4 * v + 1]) + f.y);
+              r[4 * v + 2] = __float_as_uint(__uint_as_float(r[4 * v + 2]) + f.z);
+              r[4 * v + 3] = __float_as_uint(__uint_as_float(r[4 * v + 3]) + f.w);
+            }
+          }
+        }
         const int gn = nt * BNP + c0;
+        if (row >= Np) continue;  // last row tile of an Np that is not a multiple of 256
         if (EPI == 1) {
           float* X = reinterpret_cast<float*>(pr.out) + row * ld + gn;
 #pragma unroll
@@ -750,6 +790,15 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm2(const __grid_constant__ TcP
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive_cluster(acce_l + 8 * ab);
+      if (contrib) {
+        __threadfence();
+        epi_bar();
+        if (leader) atomicExch(P.flags + me, 1);
+      } else if (finish) {
+        epi_bar();
+        if (leader)
+          for (int p2 = pair + 1; p2 <= p_last; ++p2) atomicExch(P.flags + 2 * p2 + (int)rank, 0);
+      }
     }
   }
   tc_fence_before();

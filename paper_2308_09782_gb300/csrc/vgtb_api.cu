@@ -37,7 +37,8 @@ struct HostSys {
   double omega = 0, nel = 0, dt = 0;
   std::vector<int> orb_off;
   std::vector<double> z, gamma;
-  std::vector<int> tgt_I, tgt_J, tgt_img0, img_blk, atom_tgt0;
+  std::vector<int> tgt_I, tgt_J, tgt_img0, img_blk, atom_tgt0, tgt_el0;
+  int n_el = 0;
   std::vector<long long> blk_off;
   std::vector<double> wk;
   // device
@@ -289,6 +290,11 @@ int prepare_system(vgtb_ctx* ctx, int si, const vgtb_system& s, HostSys& h, DevS
   }
   h.tgt_img0.push_back((int)h.img_blk.size());
   h.n_tgt = (int)h.tgt_I.size();
+  h.tgt_el0.assign(h.n_tgt + 1, 0);
+  for (int tg = 0; tg < h.n_tgt; ++tg)
+    h.tgt_el0[tg + 1] = h.tgt_el0[tg] + (h.orb_off[h.tgt_I[tg] + 1] - h.orb_off[h.tgt_I[tg]]) *
+                                             (h.orb_off[h.tgt_J[tg] + 1] - h.orb_off[h.tgt_J[tg]]);
+  h.n_el = h.tgt_el0[h.n_tgt];
   h.atom_tgt0.assign(s.n_atoms + 1, 0);
   for (int t = 0; t < h.n_tgt; ++t) h.atom_tgt0[h.tgt_I[t] + 1]++;
   for (int i = 0; i < s.n_atoms; ++i) h.atom_tgt0[i + 1] += h.atom_tgt0[i];
@@ -369,6 +375,13 @@ int prepare_system(vgtb_ctx* ctx, int si, const vgtb_system& s, HostSys& h, DevS
   d.wk = pd;
   TRY(upload(ctx, &pi, h.atom_tgt0.data(), h.atom_tgt0.size()));
   d.atom_tgt0 = pi;
+  TRY(upload(ctx, &pi, h.tgt_el0.data(), h.tgt_el0.size()));
+  d.tgt_el0 = pi;
+  d.n_el = h.n_el;
+  TRY(dalloc(ctx, &d.kS, (size_t)h.nk * h.n_el));
+  TRY(dalloc(ctx, &d.kH0, (size_t)h.nk * h.n_el));
+  TRY(dalloc(ctx, &d.kP, 3 * (size_t)h.nk * h.n_el));
+  TRY(dalloc(ctx, &d.obs0, 5 * (size_t)h.n_tgt));
   const size_t NN = (size_t)h.Np * h.Np;
   TRY(dalloc(ctx, &h.Sinv, NN * h.nk));
   TRY(dalloc(ctx, &h.D0, NN * h.nk));
@@ -399,6 +412,7 @@ int prepare_system(vgtb_ctx* ctx, int si, const vgtb_system& s, HostSys& h, DevS
 int build_sinv(vgtb_ctx* ctx, int si) {
   HostSys& h = ctx->sys[si];
   const size_t NN = (size_t)h.Np * h.Np;
+  for (int k = 0; k < h.nk; ++k) launch_kblocks(ctx->d_sys, si, h.n_tgt, k, ctx->stream);
   int* info = nullptr;
   TRY(dalloc(ctx, &info, 1));
   for (int k = 0; k < h.nk; ++k) {
@@ -600,6 +614,7 @@ int finish_density(vgtb_ctx* ctx, int si) {
   HostSys& h = ctx->sys[si];
   const size_t NN = (size_t)h.Np * h.Np;
   for (int k = 0; k < h.nk; ++k) launch_hermitize(h.D0 + k * NN, h.N, h.Np, ctx->stream);
+  if (ctx->delta) launch_obs0(ctx->d_sys, si, h.n_tgt, ctx->stream);
   CK(cudaGetLastError());
   std::vector<double> q;
   TRY(host_charges(ctx, si, h.D0, q));

@@ -47,6 +47,12 @@ struct DevSys {
   const double2* phase;    // [nk][n_blk] = e^{-i 2 pi k.n}
   const double* wk;        // [nk]
   const int* atom_tgt0;    // [nat+1] targets of row atom I are atom_tgt0[I]..atom_tgt0[I+1]-1
+  int n_el;                // elements over all targets (sum of n_I n_J)
+  const int* tgt_el0;      // [n_tgt+1] first element of each target
+  double2* kS;             // [nk][n_el] Bloch-summed S_k at the target elements (Eq. 7)
+  double2* kP;             // [3][nk][n_el] momentum P_k = sum e^{-ik.L} i dS/dR_J (Eq. 12)
+  double2* kH0;            // [nk][n_el] H0_k
+  double* obs0;            // [n_tgt][5] delta forms: the D0 part of the k_obs sums
   double2* Sinv;           // [nk][Np*Np]
   double2* D0;             // [nk][Np*Np]
   double2* R0;             // [nk][Np*Np] (delta forms), else null
@@ -111,6 +117,8 @@ void launch_to_planar_f32(const double2* src, float* dst, int Np, cudaStream_t s
 void launch_phase(const DevSys* sys, const DevTraj* trj, const DevItem* items, const int* warp_prefix,
                   int n_traj, int total_warps, const int* step, int mode, int fixed_step, cudaStream_t st);
 int scc_configure(int max_nat);
+void launch_kblocks(const DevSys* sys, int s_idx, int n_tgt, int k, cudaStream_t st);
+void launch_obs0(const DevSys* sys, int s_idx, int n_tgt, cudaStream_t st);
 void launch_bloch_setup(const DevSys* sys, int s_idx, int n_tgt, int k, int mode, const double* eps,
                         double2* out, cudaStream_t st);
 void launch_mulliken_setup(const DevSys* sys, int s_idx, int n_tgt, const double2* D, double* part,
