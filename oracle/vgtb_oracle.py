@@ -182,15 +182,20 @@ def setup(sysd):
     return out
 
 
+def occupied_states(H, S, n_occ):
+    """Lowest n_occ solutions of H C = S C eps (Eq. 5 at rest); returns (C_occ, eps)."""
+    e, C = sla.eigh(H, S)
+    return C[:, :n_occ], e
+
+
 def density_from_hamiltonian(H, S, n_occ):
     """D = sum_{n < n_occ} 2 C_n C_n^dagger from H C = S C eps; returns (D, eps)."""
-    e, C = sla.eigh(H, S)
-    Co = C[:, :n_occ]
+    Co, e = occupied_states(H, S, n_occ)
     return 2.0 * (Co @ Co.conj().T), e
 
 
 def ground_state(sysd, tol=1e-12, max_iter=200, mix=0.2, history=8, ctx=None):
-    """SCC ground state at A = 0 (Sec. 3.1): returns dict(D, dq, eps, gap, iters).
+    """SCC ground state at A = 0 (Sec. 3.1): returns dict(D, C, dq, eps, gap, iters).
 
     Each iteration diagonalises H_k[dq] at every k, occupies the lowest
     N_el/2 states twice and recomputes dq; dq is mixed with Anderson mixing
@@ -207,17 +212,18 @@ def ground_state(sysd, tol=1e-12, max_iter=200, mix=0.2, history=8, ctx=None):
     gap = np.inf
     for it in range(1, max_iter + 1):
         eps_orb = scc_shift(gamma, dq)[atom_of]
-        D_list = []
+        D_list, C_list = [], []
         gap = np.inf
         for S, H0, P in zip(ctx["S"], ctx["H0"], ctx["P"]):
             H = hamiltonian(H0, S, P, np.zeros(3), eps_orb)
-            D, e = density_from_hamiltonian(H, S, n_occ)
-            D_list.append(D)
+            Co, e = occupied_states(H, S, n_occ)
+            C_list.append(Co)
+            D_list.append(2.0 * (Co @ Co.conj().T))
             gap = min(gap, e[n_occ] - e[n_occ - 1])
         dq_out = mulliken(D_list, ctx["S"], ctx["wk"], atom_of) - z
         res = dq_out - dq
         if np.max(np.abs(res)) < tol or not np.any(gamma):
-            return {"D": D_list, "dq": dq_out, "eps": scc_shift(gamma, dq_out),
+            return {"D": D_list, "C": C_list, "dq": dq_out, "eps": scc_shift(gamma, dq_out),
                     "gap": gap, "iters": it, "residual": float(np.max(np.abs(res)))}
         xs.append(dq.copy())
         fs.append(res.copy())

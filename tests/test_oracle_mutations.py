@@ -12,7 +12,9 @@ import pytest
 import oracle as O
 from oracle import vgtb_oracle as ov
 from paper_2308_09782_gb300 import inputs
+from oracle import crank_nicolson as ocn
 from tests import test_oracle_pins as pins
+from tests import test_oracle_cn as cnpins
 
 C = ov.C_LIGHT
 
@@ -73,6 +75,46 @@ _orig_bloch = ov.bloch_matrices
 def _transposed_p(sysd, kred):
     S, H0, P = _orig_bloch(sysd, kred)
     return S, H0, P.transpose(0, 2, 1).copy()
+
+
+def _cn_backward(S, H, Cc, theta):
+    return np.linalg.solve(S - 1j * theta * H, (S + 1j * theta * H) @ Cc)
+
+
+def _cn_full_dt(S, H, Cc, theta):
+    return np.linalg.solve(S + 2j * theta * H, (S - 2j * theta * H) @ Cc)
+
+
+def _cn_orthogonal(S, H, Cc, theta):
+    one = np.eye(S.shape[0])
+    return np.linalg.solve(one + 1j * theta * H, (one - 1j * theta * H) @ Cc)
+
+
+def _cn_h_at_tn(A_table, n, eps_n, eps_prev):
+    return np.asarray(A_table[n], float), eps_n
+
+
+def _cn_shift_not_extrapolated(A_table, n, eps_n, eps_prev):
+    return 0.5 * (np.asarray(A_table[n], float) + np.asarray(A_table[n + 1], float)), eps_n
+
+
+@pytest.mark.parametrize("mutant,pin", [
+    (("cn_step", _cn_backward), "cn1"),
+    (("cn_step", _cn_full_dt), "cn1"),
+    (("cn_step", _cn_orthogonal), "cn2"),
+    (("cn_midpoint", _cn_h_at_tn), "cn4"),
+    (("cn_midpoint", _cn_shift_not_extrapolated), "cn4"),
+])
+def test_cn_pin_catches_planted_mistake(monkeypatch, mutant, pin):
+    monkeypatch.setattr(ocn, mutant[0], mutant[1])
+    with pytest.raises(AssertionError):
+        if pin == "cn1":
+            cnpins.test_cn1_closed_form_time_independent(cnpins.si8d_nonscc.__wrapped__())
+        elif pin == "cn2":
+            cnpins.test_cn2_unitary_in_s_metric(cnpins.si8d.__wrapped__())
+        elif pin == "cn4":
+            d = cnpins.si8d.__wrapped__()
+            cnpins.test_cn4_second_order(d, cnpins._rk4_reference(*d, 0.0125))
 
 
 @pytest.mark.parametrize("target,mutant,pin", [
