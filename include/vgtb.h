@@ -57,7 +57,18 @@ extern "C" {
 #define VGTB_SPLIT_BF16X3  1   /* delta form, tcgen05 BF16 hi/lo 3-product GEMMs, FP32 accumulate */
 
 #define VGTB_INIT_GROUND   0   /* create() computes the SCC ground state D_k(0) */
-#define VGTB_INIT_USER     1   /* caller sets D_k(0) with vgtb_set_density() */
+#define VGTB_INIT_USER     1   /* caller sets D_k(0) with vgtb_set_density() (leapfrog) or the
+                                  occupied states with vgtb_set_coefficients() (Crank-Nicolson) */
+
+#define VGTB_LEAPFROG       0  /* density matrices by Eq. 6 and the leapfrog of Eq. 13 */
+#define VGTB_CRANK_NICOLSON 1  /* occupied coefficient vectors by Eq. 5 with the unitary
+                                  Crank-Nicolson scheme named in Sec. 2:
+                                  (S + i dt/2 H(t+dt/2)) C(t+dt) = (S - i dt/2 H(t+dt/2)) C(t),
+                                  H(t+dt/2) from A((t_n + t_{n+1})/2) and the SCC shift
+                                  extrapolated as (3 eps_n - eps_{n-1})/2, without the |A|^2 S
+                                  term (an overall phase, remark after Eq. 3); the linear
+                                  system is solved by cn_iter fixed-point sweeps
+                                  Y <- C - i dt/2 S^-1 H Y, C(t+dt) = 2Y - C.  FP64 only. */
 
 typedef struct vgtb_ctx vgtb_ctx;  /* opaque; owned by the library */
 
@@ -96,6 +107,11 @@ typedef struct {
   int autotune;             /* 1 = time the GEMM tile candidates at create and keep the fastest */
   double scc_tol;           /* ground state: stop when max|dq_out - dq_in| < scc_tol (0 = 1e-11) */
   int scc_max_iter;         /* ground state iteration limit (0 = 200) */
+  int integrator;           /* VGTB_LEAPFROG (default) or VGTB_CRANK_NICOLSON */
+  int cn_iter;              /* Crank-Nicolson fixed-point sweeps per step, >= 2 (0 = 12); the
+                               sweeps contract by dt/2 max|eig(S^-1 H)| each */
+  double cn_tol;            /* Crank-Nicolson: propagate() fails with E_UNSTABLE when the last
+                               two iterates differ by more than cn_tol in any entry (0 = 1e-10) */
 } vgtb_options;
 
 /* Fill *opt with the defaults above (precision FP64, ground-state init). */
@@ -120,12 +136,26 @@ int vgtb_create_batch(vgtb_ctx** out, int n_sys, const vgtb_system* sys,
  * Errors: E_INVALID (index, non-finite entries). */
 int vgtb_set_density(vgtb_ctx* ctx, int sys_index, int k, const double* d0);
 
+/* Crank-Nicolson integrator: set the occupied states C_k(0) of system
+ * `sys_index` at k-point k.  c: host array [N][n_occ] complex interleaved,
+ * column n = state n (coefficients of Eq. 4), each occupied twice; n_occ must
+ * be N_el/2.  D_k(0) = 2 C C^dagger is formed on the device.  Once every k of
+ * the system is set, every trajectory of that system restarts from step 0.
+ * Errors: E_INVALID (not a Crank-Nicolson context, index, n_occ, non-finite). */
+int vgtb_set_coefficients(vgtb_ctx* ctx, int sys_index, int k, int n_occ, const double* c);
+
+/* Crank-Nicolson integrator: copy C_k(t_n) of trajectory `traj` into c_out
+ * ([N][n_occ] complex interleaved, caller-owned).  Errors: E_INVALID. */
+int vgtb_get_coefficients(vgtb_ctx* ctx, int traj, int k, double* c_out);
+
 /* Set the vector potential of trajectory `traj`: A[n][3] = A(t_n), n = 0 ..
  * n_times-1 (Eq. 3; a delta kick is A(t_n) = A0 for all n).  Restarts the
  * trajectory clock at step 0.  Errors: E_INVALID. */
 int vgtb_set_field(vgtb_ctx* ctx, int traj, int n_times, const double* A);
 
-/* Advance every trajectory by nsteps leapfrog steps (Eqs. 6, 10, 13, 14).
+/* Advance every trajectory by nsteps steps of the context's integrator
+ * (leapfrog: Eqs. 6, 10, 13, 14; Crank-Nicolson: Eq. 5 with the same
+ * observables from D_k = 2 C C^dagger).
  * Observables of every visited time level are stored on the device.
  * Errors: E_STATE (no density / field, or the field table ends before step
  * n+nsteps), E_UNSTABLE, E_TIMEOUT, E_CUDA. */
@@ -170,7 +200,8 @@ int vgtb_spectrum(vgtb_ctx* ctx, int traj, int n0, int n1, double e0, double tau
 int vgtb_group_charges(vgtb_ctx* ctx, int traj, int n_groups, const int* group, double* out);
 
 /* Checkpoint: the state is D_k(t_n), D_k(t_{n-1}) of every trajectory and k,
- * plus n.  vgtb_state_size() gives the byte size of the host buffer. */
+ * plus n (Crank-Nicolson: C_k(t_n) and the SCC shifts of levels n, n-1).
+ * vgtb_state_size() gives the byte size of the host buffer. */
 long long vgtb_state_size(const vgtb_ctx* ctx);
 int vgtb_get_state(vgtb_ctx* ctx, void* buf, long long bytes);
 int vgtb_set_state(vgtb_ctx* ctx, const void* buf, long long bytes);
@@ -178,7 +209,10 @@ int vgtb_set_state(vgtb_ctx* ctx, const void* buf, long long bytes);
 /* Kernel timing: with enable = 1, propagate() records CUDA events around the
  * hot kernels on the context stream and accumulates their device time.
  * vgtb_kernel_stats() copies, for kernel classes 0..n-1 (see VGTB_K_*),
- * launches[i] and total milliseconds ms[i], and returns the class count. */
+ * launches[i] and total milliseconds ms[i], and returns the class count.
+ * Crank-Nicolson contexts use the same classes for: OBS = D = 2 C C^dagger and
+ * the sums, GEMM1 = S^-1 H(t+dt/2), GEMM2 = the fixed-point sweeps, LEAP = the
+ * convergence check and the step counter. */
 #define VGTB_K_OBS     0   /* charges / current / energy partial sums (Eqs. 10, 14) */
 #define VGTB_K_SCC     1   /* dq, eps = gamma dq, finalised observables */
 #define VGTB_K_PHASE   2   /* Bloch sum of H_k(t) with A(t) (Eqs. 7-12) */

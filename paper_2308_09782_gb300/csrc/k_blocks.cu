@@ -216,11 +216,109 @@ void launch_obs0(const DevSys* sys, int s_idx, int n_tgt, cudaStream_t st) {
   k_obs0<<<blocks, threads, 0, st>>>(sys, s_idx);
 }
 
+__device__ __forceinline__ float half_sum_f(float v) {
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// k_obs of the split form: the dD sums in FP32 (dD converted from the FP64
+// master with integer operations, k-space blocks as packed FP32 records), the
+// constant D0 part (obs0) and the A terms in FP64.  The FP32 rounding of the
+// dD part is far below the BF16x3 products' own error.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_obs_split(const DevSys* __restrict__ sysv, const DevTraj* __restrict__ trj,
+                                                   const DevItem* __restrict__ items, const int* __restrict__ wpre,
+                                                   int n_traj, int total, const int* __restrict__ step,
+                                                   int fixed_step) {
+  const Unit U = unit_of(wpre, n_traj, total);
+  const int lane = threadIdx.x & 15;
+  float sS = 0.f, sx = 0.f, sy = 0.f, sz = 0.f, sH = 0.f;
+  const DevTraj& T = trj[U.t];
+  const DevSys& S = sysv[T.sys];
+  int n = 0;
+  if (U.active) {
+    n = fixed_step >= 0 ? fixed_step : *step;
+    const int par = n & 1;
+    const int I = S.tgt_I[U.tg], J = S.tgt_J[U.tg];
+    const int oi = S.orb_off[I];
+    const int oj = S.orb_off[J], nj = S.orb_off[J + 1] - oj;
+    const int el0 = S.tgt_el0[U.tg], nel = S.tgt_el0[U.tg + 1] - el0;
+    for (int k = 0; k < S.nk; ++k) {
+      const double2* Dk = items[T.item0 + k].D[par];
+      const float4* kb = S.kf + 3 * ((long long)k * S.n_el + el0);
+      float lS = 0.f, lx = 0.f, ly = 0.f, lz = 0.f, lH = 0.f;
+      for (int e = lane; e < nel; e += 16) {
+        const int a = e / nj, b = e - a * nj;
+        const double2 dd = Dk[(long long)(oi + a) * S.Np + (oj + b)];
+        const float dr = d2f_bits(dd.x), di = d2f_bits(dd.y);
+        const float4 c0 = kb[3 * e], c1 = kb[3 * e + 1], c2 = kb[3 * e + 2];
+        lS = fmaf(dr, c0.x, fmaf(di, c0.y, lS));
+        lx = fmaf(dr, c0.z, fmaf(di, c0.w, lx));
+        ly = fmaf(dr, c1.x, fmaf(di, c1.y, ly));
+        lz = fmaf(dr, c1.z, fmaf(di, c1.w, lz));
+        lH = fmaf(dr, c2.x, fmaf(di, c2.y, lH));
+      }
+      const float wk = S.wkf[k];
+      sS = fmaf(wk, lS, sS);
+      sx = fmaf(wk, lx, sx);
+      sy = fmaf(wk, ly, sy);
+      sz = fmaf(wk, lz, sz);
+      sH = fmaf(wk, lH, sH);
+    }
+  }
+  sS = half_sum_f(sS);
+  sx = half_sum_f(sx);
+  sy = half_sum_f(sy);
+  sz = half_sum_f(sz);
+  sH = half_sum_f(sH);
+  if (U.active && lane == 0) {
+    const double* o = S.obs0 + 5LL * U.tg;
+    const double dS = o[0] + f2d_bits(sS), dx = o[1] + f2d_bits(sx), dy = o[2] + f2d_bits(sy);
+    const double dz = o[3] + f2d_bits(sz), dH = o[4] + f2d_bits(sH);
+    double A0 = 0.0, A1 = 0.0, A2 = 0.0;
+    if (T.A) {
+      A0 = T.A[3 * n];
+      A1 = T.A[3 * n + 1];
+      A2 = T.A[3 * n + 2];
+    }
+    constexpr double ic = 1.0 / kLight;
+    const double a0 = A0 * ic, a1 = A1 * ic, a2 = A2 * ic;
+    const double alpha = 0.5 * (a0 * a0 + a1 * a1 + a2 * a2);
+    double* p = T.part + 5LL * U.tg;
+    p[0] = dS;
+    p[1] = dx + a0 * dS;
+    p[2] = dy + a1 * dS;
+    p[3] = dz + a2 * dS;
+    p[4] = dH + (a0 * dx + a1 * dy + a2 * dz) + alpha * dS;
+  }
+}
+
 void launch_obs(const DevSys* sys, const DevTraj* trj, const DevItem* items, const int* warp_prefix,
                 int n_traj, int total_units, const int* step, int delta, int fixed_step, cudaStream_t st) {
   const int threads = 256;
   const int blocks = (total_units * 16 + threads - 1) / threads;
-  k_obs<<<blocks, threads, 0, st>>>(sys, trj, items, warp_prefix, n_traj, total_units, step, delta, fixed_step);
+  if (delta == 2)
+    k_obs_split<<<blocks, threads, 0, st>>>(sys, trj, items, warp_prefix, n_traj, total_units, step, fixed_step);
+  else
+    k_obs<<<blocks, threads, 0, st>>>(sys, trj, items, warp_prefix, n_traj, total_units, step, delta, fixed_step);
+}
+
+// Setup (split form): packed FP32 copies of the k-space blocks for k_obs_split.
+__global__ void k_kblocks_f32(const DevSys* __restrict__ sysv, int s_idx, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;  // over nk * n_el
+  const DevSys& S = sysv[s_idx];
+  if (i >= n) return;
+  const long long ps = (long long)S.nk * S.n_el;
+  const double2 s = S.kS[i], px = S.kP[i], py = S.kP[ps + i], pz = S.kP[2 * ps + i], h = S.kH0[i];
+  S.kf[3 * i] = make_float4((float)s.x, (float)s.y, (float)px.x, (float)px.y);
+  S.kf[3 * i + 1] = make_float4((float)py.x, (float)py.y, (float)pz.x, (float)pz.y);
+  S.kf[3 * i + 2] = make_float4((float)h.x, (float)h.y, 0.f, 0.f);
+}
+
+void launch_kblocks_f32(const DevSys* sys, int s_idx, long long n, cudaStream_t st) {
+  k_kblocks_f32<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(sys, s_idx, n);
 }
 
 // ---------------------------------------------------------------------------
@@ -232,27 +330,9 @@ void launch_obs(const DevSys* sys, const DevTraj* trj, const DevItem* items, con
 //                of a trajectory adds up J (Eq. 14), the band energy and
 //                dq.eps/2 in a fixed order and runs the checks.
 // ---------------------------------------------------------------------------
-constexpr int kSccThreads = 256;
-constexpr int kSccRows = 8;
+constexpr int kSccThreads = 128;
+constexpr int kSccRows = kSccThreads / 32;
 constexpr int kAtomsPerCta = kSccThreads / 32;
-
-template <int NT>
-__device__ void block_sum5(double (&v)[5], double* sh) {
-  const int tid = threadIdx.x;
-#pragma unroll
-  for (int i = 0; i < 5; ++i) sh[i * NT + tid] = v[i];
-  __syncthreads();
-  for (int s = NT / 2; s > 0; s >>= 1) {
-    if (tid < s) {
-#pragma unroll
-      for (int i = 0; i < 5; ++i) sh[i * NT + tid] += sh[i * NT + tid + s];
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int i = 0; i < 5; ++i) v[i] = sh[i * NT];
-  __syncthreads();
-}
 
 __global__ void __launch_bounds__(kSccThreads) k_scc_atoms(const DevSys* __restrict__ sysv, DevTraj* trj, int n_traj,
                                                           int nblk, const int* __restrict__ step, int stride,
@@ -286,7 +366,8 @@ __global__ void __launch_bounds__(kSccThreads) k_scc_atoms(const DevSys* __restr
 __global__ void __launch_bounds__(kSccThreads) k_scc_eps(const DevSys* __restrict__ sysv, DevTraj* trj, int n_traj,
                                                         int nblk, const int* __restrict__ step, int fixed_step,
                                                         int record) {
-  extern __shared__ double sm[];  // [kSccThreads*5] reduction + [nat] dq
+  constexpr int NW = kSccThreads / 32;
+  __shared__ double red[6][NW];
   __shared__ int s_last;
   const int t = blockIdx.x / nblk, b = blockIdx.x % nblk;
   if (t >= n_traj) return;
@@ -295,21 +376,27 @@ __global__ void __launch_bounds__(kSccThreads) k_scc_eps(const DevSys* __restric
   const int myblk = (S.nat + kSccRows - 1) / kSccRows;
   if (b >= myblk) return;
   const int n = fixed_step >= 0 ? fixed_step : *step;
-  double* red = sm;
-  double* dq = sm + 5 * kSccThreads;
-  const int tid = threadIdx.x;
-  for (int I = tid; I < S.nat; I += kSccThreads) dq[I] = T.dq[I];
-  __syncthreads();
-  const int warp = tid >> 5, lane = tid & 31;
-  const int r0 = b * kSccRows, r1 = min(S.nat, r0 + kSccRows);
-  for (int I = r0 + warp; I < r1; I += kSccThreads / 32) {
-    double e = 0.0;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int I = b * kSccRows + warp;  // one warp per row of gamma
+  if (I < S.nat) {
     const double* g = S.gamma + (long long)I * S.nat;
-    for (int K = lane; K < S.nat; K += 32) e += g[K] * dq[K];
-    e = warp_sum(e);
+    const double* dq = T.dq;
+    // four independent partial sums keep four loads in flight per lane
+    double e0 = 0.0, e1 = 0.0, e2 = 0.0, e3 = 0.0;
+    int K = lane;
+    for (; K + 96 < S.nat; K += 128) {
+      e0 += g[K] * dq[K];
+      e1 += g[K + 32] * dq[K + 32];
+      e2 += g[K + 64] * dq[K + 64];
+      e3 += g[K + 96] * dq[K + 96];
+    }
+    for (; K < S.nat; K += 32) e0 += g[K] * dq[K];
+    const double e = warp_sum((e0 + e1) + (e2 + e3));
     if (lane == 0) {
       T.eps[I] = e;
       T.erow[I] = dq[I] * e;
+      if (T.eps_lv) T.eps_lv[(long long)(n & 1) * S.nat + I] = e;
+      __threadfence();
     }
   }
   // last CTA of this trajectory: J, E and the checks in a fixed order
@@ -321,23 +408,31 @@ __global__ void __launch_bounds__(kSccThreads) k_scc_eps(const DevSys* __restric
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  double v[5] = {0, 0, 0, 0, 0};  // Tx, Ty, Tz, E_band, dq.eps
-  double qsum = 0.0;
-  for (int I = tid; I < S.nat; I += kSccThreads) {
-    const double* a = T.apart + 4LL * I;
+  double v[6] = {0, 0, 0, 0, 0, 0};  // Tx, Ty, Tz, E_band, dq.eps, electron count
+  for (int J = tid; J < S.nat; J += kSccThreads) {
+    const double* a = T.apart + 4LL * J;
     v[0] += a[0];
     v[1] += a[1];
     v[2] += a[2];
     v[3] += a[3];
-    v[4] += T.erow[I];
-    qsum += dq[I] + S.z[I];
+    v[4] += T.erow[J];
+    v[5] += T.dq[J] + S.z[J];
   }
-  block_sum5<kSccThreads>(v, red);
-  double w[5] = {qsum, 0, 0, 0, 0};
-  block_sum5<kSccThreads>(w, red);
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    v[i] = warp_sum(v[i]);
+    if (lane == 0) red[i][warp] = v[i];
+  }
+  __syncthreads();
   if (tid == 0) {
-    const double J0 = -v[0] / S.omega, J1 = -v[1] / S.omega, J2 = -v[2] / S.omega;
-    const double E = v[3] + 0.5 * v[4];
+    double w[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      w[i] = red[i][0];
+      for (int q = 1; q < NW; ++q) w[i] += red[i][q];
+    }
+    const double J0 = -w[0] / S.omega, J1 = -w[1] / S.omega, J2 = -w[2] / S.omega;
+    const double E = w[3] + 0.5 * w[4];
     if (record) {
       T.J[3LL * n] = J0;
       T.J[3LL * n + 1] = J1;
@@ -345,19 +440,15 @@ __global__ void __launch_bounds__(kSccThreads) k_scc_eps(const DevSys* __restric
       T.E[n] = E;
     }
     int st = 0;
-    if (!isfinite(J0) || !isfinite(J1) || !isfinite(J2) || !isfinite(E) || !isfinite(w[0])) st |= ST_NONFINITE;
-    if (fabs(w[0] - S.nel) > 1e-6 * fmax(1.0, S.nel)) st |= ST_DRIFT;
+    if (!isfinite(J0) || !isfinite(J1) || !isfinite(J2) || !isfinite(E) || !isfinite(w[5])) st |= ST_NONFINITE;
+    if (fabs(w[5] - S.nel) > 1e-6 * fmax(1.0, S.nel)) st |= ST_DRIFT;
     if (st) atomicOr(T.status, st);
     *T.ticket = 0;
   }
 }
 
 int scc_configure(int max_nat) {
-  const size_t sm = sizeof(double) * (5 * kSccThreads + (size_t)max_nat);
-  if (sm > 48 * 1024) {
-    if (cudaFuncSetAttribute(k_scc_eps, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
-      return -1;
-  }
+  (void)max_nat;  // the reduction needs no dynamic shared memory
   return 0;
 }
 
@@ -366,8 +457,7 @@ void launch_scc(const DevSys* sys, DevTraj* trj, int n_traj, const int* step, in
   const int nblk_a = (max_nat + kAtomsPerCta - 1) / kAtomsPerCta;
   k_scc_atoms<<<n_traj * nblk_a, kSccThreads, 0, st>>>(sys, trj, n_traj, nblk_a, step, stride, fixed_step, record);
   const int nblk = (max_nat + kSccRows - 1) / kSccRows;
-  const size_t sm = sizeof(double) * (5 * kSccThreads + (size_t)max_nat);
-  k_scc_eps<<<n_traj * nblk, kSccThreads, sm, st>>>(sys, trj, n_traj, nblk, step, fixed_step, record);
+  k_scc_eps<<<n_traj * nblk, kSccThreads, 0, st>>>(sys, trj, n_traj, nblk, step, fixed_step, record);
 }
 
 // ---------------------------------------------------------------------------
@@ -375,6 +465,9 @@ void launch_scc(const DevSys* sys, DevTraj* trj, int n_traj, const int* step, in
 //   plain: v = H0 + (alpha + (eps_I + eps_J)/2) S + (i/c) A.dS        (Eqs. 9-12)
 //   delta: H without alpha (its commutator vanishes, remark after Eq. 3) and
 //          dH = ((eps_I-eps0_I) + (eps_J-eps0_J))/2 S + (i/c) A.dS.
+//   CN:    H(t_{n+1/2}) without alpha (an overall phase of the states, remark
+//          after Eq. 3) from A_{n+1/2} = (A_n + A_{n+1})/2 and the shift
+//          extrapolated from the two latest levels, (3 eps_n - eps_{n-1})/2.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_phase(const DevSys* __restrict__ sysv, const DevTraj* __restrict__ trj,
                                                const DevItem* __restrict__ items, const int* __restrict__ wpre,
@@ -391,6 +484,11 @@ __global__ void __launch_bounds__(256) k_phase(const DevSys* __restrict__ sysv, 
     A0 = T.A[3 * n];
     A1 = T.A[3 * n + 1];
     A2 = T.A[3 * n + 2];
+    if (mode == PH_FP64_CN) {  // A(t_{n+1/2}) = (A_n + A_{n+1}) / 2
+      A0 = 0.5 * (A0 + T.A[3 * n + 3]);
+      A1 = 0.5 * (A1 + T.A[3 * n + 4]);
+      A2 = 0.5 * (A2 + T.A[3 * n + 5]);
+    }
   }
   const double ic = 1.0 / kLight;
   const double alpha = (A0 * A0 + A1 * A1 + A2 * A2) * 0.5 * ic * ic;
@@ -399,7 +497,14 @@ __global__ void __launch_bounds__(256) k_phase(const DevSys* __restrict__ sysv, 
   const int oj = S.orb_off[J], nj = S.orb_off[J + 1] - oj;
   const int nel = ni * nj;
   const int g0 = S.tgt_img0[U.tg], g1 = S.tgt_img0[U.tg + 1];
-  const double ebar = 0.5 * (T.eps[I] + T.eps[J]);
+  double eI = T.eps[I], eJ = T.eps[J];
+  if (mode == PH_FP64_CN && n > 0) {  // eps(t_{n+1/2}) = (3 eps_n - eps_{n-1}) / 2
+    const double* cur = T.eps_lv + (long long)(n & 1) * S.nat;
+    const double* prv = T.eps_lv + (long long)((n - 1) & 1) * S.nat;
+    eI = 1.5 * cur[I] - 0.5 * prv[I];
+    eJ = 1.5 * cur[J] - 0.5 * prv[J];
+  }
+  const double ebar = 0.5 * (eI + eJ);
   const double beta = (mode == PH_FP64_PLAIN) ? alpha + ebar : ebar;
   const double dbeta = (mode == PH_FP64_PLAIN) ? 0.0 : 0.5 * ((T.eps[I] - S.eps0[I]) + (T.eps[J] - S.eps0[J]));
   for (int k = 0; k < S.nk; ++k) {

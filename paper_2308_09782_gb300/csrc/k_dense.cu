@@ -8,6 +8,8 @@
 //                read and written exactly once.
 //   helpers    - Hermitian fill, eigenvector transpose, BF16 hi/lo splitting.
 // GB300 has no FP64 tensor-core kind, so the FP64 path runs on DFMA.
+#include <algorithm>
+
 #include "vgtb_internal.h"
 
 namespace vgtb {
@@ -36,14 +38,30 @@ __global__ void __launch_bounds__(256) k_gemm_f64(const GemmF64Item* __restrict_
     const double2* A = it.A[sg] + par * it.a_par[sg];
     const double2* R = it.R[sg];
     const int K = it.K[sg], lda = it.lda[sg], ldr = it.ldr[sg];
+    const bool ta = it.conj_t & 1, tr = (it.conj_t >> 1) & 1;
     for (int k0 = 0; k0 < K; k0 += GK) {
-      // load 64 x 16 of A and of R: thread -> (row = tid/16 + 16 p, col = tid%16)
+      // load 64 x 16 of A and of R: thread -> (row = tid/16 + 16 p, col = tid%16);
+      // a conjugate-transposed operand is read along its rows instead (coalesced)
 #pragma unroll
       for (int p = 0; p < 4; ++p) {
         const int r = ty + 16 * p, c = tx;
-        const int gm = m0 + r, gn = n0 + r, gk = k0 + c;
-        As[c][r] = (gm < it.M && gk < K) ? A[(long long)gm * lda + gk] : make_double2(0.0, 0.0);
-        Rs[c][r] = (gn < it.N && gk < K) ? R[(long long)gn * ldr + gk] : make_double2(0.0, 0.0);
+        const int idx = tid + 256 * p, tk = idx >> 6, trw = idx & 63;
+        if (ta) {
+          const int gm = m0 + trw, gk = k0 + tk;
+          const double2 v = (gm < it.M && gk < K) ? A[(long long)gk * lda + gm] : make_double2(0.0, 0.0);
+          As[tk][trw] = make_double2(v.x, -v.y);
+        } else {
+          const int gm = m0 + r, gk = k0 + c;
+          As[c][r] = (gm < it.M && gk < K) ? A[(long long)gm * lda + gk] : make_double2(0.0, 0.0);
+        }
+        if (tr) {
+          const int gn = n0 + trw, gk = k0 + tk;
+          const double2 v = (gn < it.N && gk < K) ? R[(long long)gk * ldr + gn] : make_double2(0.0, 0.0);
+          Rs[tk][trw] = make_double2(v.x, -v.y);
+        } else {
+          const int gn = n0 + r, gk = k0 + c;
+          Rs[c][r] = (gn < it.N && gk < K) ? R[(long long)gn * ldr + gk] : make_double2(0.0, 0.0);
+        }
       }
       __syncthreads();
 #pragma unroll 4
@@ -74,7 +92,18 @@ __global__ void __launch_bounds__(256) k_gemm_f64(const GemmF64Item* __restrict_
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int gn = n0 + tx + 16 * j;
-      if (gn < it.N) it.C[(long long)gm * it.ldc + gn] = make_double2(cr[i][j], ci[i][j]);
+      if (gn >= it.N) continue;
+      double2 v = make_double2(cr[i][j], ci[i][j]);
+      if (it.epi == 1) {
+        const double2 c = it.coef;
+        v = make_double2(c.x * v.x - c.y * v.y, c.x * v.y + c.y * v.x);
+        if (it.base) {
+          const double2 b = it.base[(long long)gm * it.ldb + gn];
+          v.x += b.x;
+          v.y += b.y;
+        }
+      }
+      it.C[(long long)gm * it.ldc + gn] = v;
     }
   }
 }
@@ -193,38 +222,6 @@ void launch_leap(const LeapItem* items, int n_items, int Np_max, int x_f32, cons
   dim3 grid(nt * (nt + 1) / 2, n_items);
   dim3 block(LT, 8);
   k_leap<<<grid, block, 0, st>>>(items, step, dt, counter, step_rw);
-}
-
-// ---------------------------------------------------------------------------
-// IEEE-754 float <-> double conversions done with integer bit operations.
-// GB300 runs FP64 instructions, conversions included, at a small fraction of
-// the integer rate, so the split leapfrog keeps only its two FP64 FMAs on the
-// FP64 pipe.  float -> double is exact (signed zero for float zeros and
-// subnormals, which are below 1.2e-38); double -> float rounds to nearest even
-// and flushes magnitudes below 2^-126 to signed zero and above the float range
-// to infinity.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ double f2d_bits(float f) {
-  const uint32_t u = __float_as_uint(f);
-  const uint32_t e = (u >> 23) & 0xffu;
-  const uint32_t sign = u & 0x80000000u;
-  const uint32_t ee = (e == 255u) ? 2047u : e + 896u;  // exponent bias 1023 - 127
-  const uint32_t hi = (e == 0u) ? sign : (sign | (ee << 20) | ((u >> 3) & 0xfffffu));
-  const uint32_t lo = (e == 0u) ? 0u : (u << 29);
-  return __hiloint2double((int)hi, (int)lo);
-}
-
-__device__ __forceinline__ float d2f_bits(double d) {
-  const uint32_t hi = (uint32_t)__double2hiint(d), lo = (uint32_t)__double2loint(d);
-  const uint32_t sign = hi & 0x80000000u;
-  const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
-  const uint32_t mant = ((hi & 0xfffffu) << 3) | (lo >> 29);
-  const uint32_t rest = lo & 0x1fffffffu;
-  uint32_t f = sign | ((uint32_t)e << 23) | mant;
-  f += (rest > 0x10000000u || (rest == 0x10000000u && (mant & 1u))) ? 1u : 0u;
-  f = (e <= 0) ? sign : f;
-  f = (e >= 255) ? (sign | 0x7f800000u) : f;
-  return __uint_as_float(f);
 }
 
 // ---------------------------------------------------------------------------
@@ -448,6 +445,52 @@ __global__ void k_hermitize(double2* a, int n, int ld) {
 void launch_hermitize(double2* a, int n, int ld, cudaStream_t st) {
   const long long tot = (long long)n * n;
   k_hermitize<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(a, n, ld);
+}
+
+// ---------------------------------------------------------------------------
+// Crank-Nicolson helpers
+// ---------------------------------------------------------------------------
+// Sets ST_CN_NOCONV on the item's trajectory when max |a - b| > tol: the last
+// two fixed-point iterates still differ, so the sweep count is too small for
+// this dt (or the iteration diverges, dt |S^-1 H| / 2 >= 1).
+__global__ void k_cn_check(const CnCheckItem* __restrict__ items, const DevTraj* __restrict__ trj, double tol) {
+  const CnCheckItem& it = items[blockIdx.y];
+  const long long tot = (long long)it.rows * it.cols;
+  double m = 0.0;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(e / it.cols), c = (int)(e - (long long)r * it.cols);
+    const double2 x = it.a[(long long)r * it.ld + c], y = it.b[(long long)r * it.ld + c];
+    m = fmax(m, fmax(fabs(x.x - y.x), fabs(x.y - y.y)));
+  }
+  // a NaN difference also counts as not converged
+  if (!(m <= tol)) atomicOr(trj[it.traj].status, ST_CN_NOCONV);
+}
+
+void launch_cn_check(const CnCheckItem* items, int n_items, int max_elems, const DevTraj* trj, double tol,
+                     cudaStream_t st) {
+  const int blocks = std::min(64, (max_elems + 255) / 256);
+  k_cn_check<<<dim3(blocks > 0 ? blocks : 1, n_items), 256, 0, st>>>(items, trj, tol);
+}
+
+__global__ void k_conj_t(const double2* src, int lds, double2* dst, int ldd, int rows, int cols) {
+  __shared__ double2 tile[32][33];
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  for (int y = threadIdx.y; y < 32; y += 8) {
+    const int sr = c0 + y, sc = r0 + threadIdx.x;  // src row = dst column
+    if (sr < cols && sc < rows) tile[y][threadIdx.x] = src[(long long)sr * lds + sc];
+  }
+  __syncthreads();
+  for (int y = threadIdx.y; y < 32; y += 8) {
+    const int dr = r0 + y, dc = c0 + threadIdx.x;
+    if (dr < rows && dc < cols) {
+      const double2 v = tile[threadIdx.x][y];
+      dst[(long long)dr * ldd + dc] = make_double2(v.x, -v.y);
+    }
+  }
+}
+
+void launch_conj_transpose(const double2* src, int lds, double2* dst, int ldd, int rows, int cols, cudaStream_t st) {
+  k_conj_t<<<dim3((cols + 31) / 32, (rows + 31) / 32), dim3(32, 8), 0, st>>>(src, lds, dst, ldd, rows, cols);
 }
 
 __global__ void k_inc(int* s) { *s += 1; }

@@ -50,6 +50,7 @@ struct HostSys {
   __nv_bfloat16* Sinv_p = nullptr;
   __nv_bfloat16* D0_p = nullptr;
   float* R0f = nullptr;
+  double2* C0d = nullptr;   // Crank-Nicolson: [nk][nocc][Np] initial states as rows (C^dagger)
   std::vector<double> dq0_h, eps0_h;
   bool density_set = false;
   std::vector<int> trajs;  // trajectories of this system
@@ -65,6 +66,7 @@ struct HostTraj {
   double* q = nullptr;
   double* dq = nullptr;
   double* eps = nullptr;
+  double* eps_lv = nullptr;
   double* part = nullptr;
   double* erow = nullptr;
   double* apart = nullptr;
@@ -92,7 +94,13 @@ struct vgtb_ctx {
   int* d_step = nullptr;
   int* d_counter = nullptr;
   int n_done = 0;
-  bool split = false, delta = false;
+  bool split = false, delta = false, cn = false;
+  // Crank-Nicolson work lists: density, M = S^-1 H, the fixed-point sweeps, the check
+  GemmF64Item* d_gD = nullptr;
+  GemmF64Item* d_gM = nullptr;
+  std::vector<GemmF64Item*> sweep;  // device list of sweep j = 1..cn_iter
+  CnCheckItem* d_cnchk = nullptr;
+  int max_nocc = 0;
   // FP64 GEMM / leap work lists
   GemmF64Item* d_g1 = nullptr;
   GemmF64Item* d_g2 = nullptr;
@@ -200,7 +208,8 @@ int prepare_system(vgtb_ctx* ctx, int si, const vgtb_system& s, HostSys& h, DevS
   if (need_ground) {
     const double half = 0.5 * s.n_electrons;
     if (std::fabs(half - std::round(half)) > 1e-12)
-      return fail(ctx, VGTB_E_INVALID, "system %d: ground state needs an even electron count", si);
+      return fail(ctx, VGTB_E_INVALID, "system %d: the ground state and the Crank-Nicolson states need an even "
+                  "electron count", si);
     h.nocc = (int)std::llround(half);
   }
   h.dt = s.dt;
@@ -381,6 +390,13 @@ int prepare_system(vgtb_ctx* ctx, int si, const vgtb_system& s, HostSys& h, DevS
   TRY(dalloc(ctx, &d.kS, (size_t)h.nk * h.n_el));
   TRY(dalloc(ctx, &d.kH0, (size_t)h.nk * h.n_el));
   TRY(dalloc(ctx, &d.kP, 3 * (size_t)h.nk * h.n_el));
+  if (ctx->split) {
+    TRY(dalloc(ctx, &d.kf, 3 * (size_t)h.nk * h.n_el));
+    std::vector<float> wf(h.wk.begin(), h.wk.end());
+    float* pwf;
+    TRY(upload(ctx, &pwf, wf.data(), wf.size()));
+    d.wkf = pwf;
+  }
   TRY(dalloc(ctx, &d.obs0, 5 * (size_t)h.n_tgt));
   const size_t NN = (size_t)h.Np * h.Np;
   TRY(dalloc(ctx, &h.Sinv, NN * h.nk));
@@ -388,6 +404,7 @@ int prepare_system(vgtb_ctx* ctx, int si, const vgtb_system& s, HostSys& h, DevS
   TRY(dalloc(ctx, &h.dq0, h.nat));
   TRY(dalloc(ctx, &h.eps0, h.nat));
   if (ctx->delta) TRY(dalloc(ctx, &h.R0, NN * h.nk));
+  if (ctx->cn) TRY(dalloc(ctx, &h.C0d, (size_t)h.nk * h.nocc * h.Np));
   if (ctx->split) {
     TRY(dalloc(ctx, &h.Sinv_p, 4 * NN * h.nk));
     TRY(dalloc(ctx, &h.D0_p, 4 * NN * h.nk));
@@ -413,6 +430,7 @@ int build_sinv(vgtb_ctx* ctx, int si) {
   HostSys& h = ctx->sys[si];
   const size_t NN = (size_t)h.Np * h.Np;
   for (int k = 0; k < h.nk; ++k) launch_kblocks(ctx->d_sys, si, h.n_tgt, k, ctx->stream);
+  if (ctx->split) launch_kblocks_f32(ctx->d_sys, si, (long long)h.nk * h.n_el, ctx->stream);
   int* info = nullptr;
   TRY(dalloc(ctx, &info, 1));
   for (int k = 0; k < h.nk; ++k) {
@@ -548,6 +566,11 @@ int ground_state(vgtb_ctx* ctx, int si) {
       if (hinfo != 0) return fail(ctx, VGTB_E_CUDA, "cusolverDnZhegvd info %d", hinfo);
       if (h.nocc < h.N && ev[h.nocc] - ev[h.nocc - 1] < 1e-8)
         return fail(ctx, VGTB_E_NO_GAP, "system %d: no gap at N_el/2 at k=%d (%.3e Ha)", si, k, ev[h.nocc] - ev[h.nocc - 1]);
+      // Crank-Nicolson keeps the occupied states: row n of the solver output is
+      // conj(C_n), i.e. the rows of C^dagger
+      if (ctx->cn)
+        CK(cudaMemcpy2DAsync(h.C0d + (size_t)k * h.nocc * h.Np, sizeof(double2) * h.Np, Hb, sizeof(double2) * h.Np,
+                             sizeof(double2) * h.N, h.nocc, cudaMemcpyDeviceToDevice, ctx->stream));
       // D_k = 2 V V^dagger over the occupied eigenvectors
       launch_vt_from_evecs(Hb, Vt, h.N, h.nocc, h.Np, ctx->stream);
       gi.A[0] = Vt;
@@ -687,6 +710,9 @@ int reset_all(vgtb_ctx* ctx) {
       CK(cudaMemsetAsync(it.D[0], 0, NN * sizeof(double2), ctx->stream));
     else
       CK(cudaMemcpyAsync(it.D[0], h.D0 + it.k * NN, NN * sizeof(double2), cudaMemcpyDeviceToDevice, ctx->stream));
+    if (ctx->cn)
+      CK(cudaMemcpyAsync(it.Cd, h.C0d + (size_t)it.k * h.nocc * h.Np, (size_t)h.nocc * h.Np * sizeof(double2),
+                         cudaMemcpyDeviceToDevice, ctx->stream));
     if (it.dD_p) CK(cudaMemsetAsync(it.dD_p, 0, 4 * NN * sizeof(__nv_bfloat16), ctx->stream));
   }
   for (auto& t : ctx->trj) CK(cudaMemsetAsync(t.status, 0, sizeof(int), ctx->stream));
@@ -712,6 +738,7 @@ int upload_traj_table(vgtb_ctx* ctx) {
     d.q = h.q;
     d.dq = h.dq;
     d.eps = h.eps;
+    d.eps_lv = h.eps_lv;
     d.part = h.part;
     d.erow = h.erow;
     d.apart = h.apart;
@@ -732,6 +759,108 @@ void drop_graph(vgtb_ctx* ctx) {
 // one step for every trajectory; ev != nullptr records 7 timing events (as
 // external event nodes when the stream is being captured into a graph)
 // ---------------------------------------------------------------------------
+// Work lists of the Crank-Nicolson step.  With Y_0 = C, sweep j = 1..m-1
+// writes Y_j = C + i (dt/2) Y_{j-1} M^dagger (in the dagger layout) into
+// Y[j & 1]; sweep m writes 2 Y_m - C = C + i dt Y_{m-1} M^dagger over C in place.
+int build_cn_lists(vgtb_ctx* ctx) {
+  const int m = ctx->opt.cn_iter, n = ctx->n_items;
+  const double theta = 0.5 * ctx->sys[0].dt;
+  std::vector<GemmF64Item> gD(n), gM(n);
+  std::vector<std::vector<GemmF64Item>> gs(m, std::vector<GemmF64Item>(n));
+  std::vector<CnCheckItem> ck(n);
+  for (int i = 0; i < n; ++i) {
+    const DevItem& it = ctx->items_h[i];
+    const HostSys& h = ctx->sys[it.sys];
+    const size_t NN = (size_t)h.Np * h.Np;
+    GemmF64Item d{};  // D = 2 C C^dagger: both operands are read as conj-transposed rows of C^dagger
+    d.A[0] = it.Cd;
+    d.R[0] = it.Cd;
+    d.K[0] = h.nocc;
+    d.lda[0] = d.ldr[0] = h.Np;
+    d.nseg = 1;
+    d.conj_t = 3;
+    d.M = d.N = d.ldc = h.Np;
+    d.C = it.D[0];
+    d.epi = 1;
+    d.coef = make_double2(2.0, 0.0);
+    gD[i] = d;
+    GemmF64Item mm{};  // M = S^-1 H = S^-1 (H^dagger)
+    mm.A[0] = h.Sinv + it.k * NN;
+    mm.R[0] = it.H;
+    mm.K[0] = h.Np;
+    mm.lda[0] = mm.ldr[0] = h.Np;
+    mm.nseg = 1;
+    mm.M = mm.N = mm.ldc = h.Np;
+    mm.C = it.W;
+    gM[i] = mm;
+    for (int j = 1; j <= m; ++j) {
+      GemmF64Item s{};  // out = C^dagger + coef (Y^dagger M^dagger)
+      s.A[0] = (j == 1) ? it.Cd : it.Y[(j - 1) & 1];
+      s.R[0] = it.W;
+      s.K[0] = h.Np;
+      s.lda[0] = s.ldr[0] = h.Np;
+      s.nseg = 1;
+      s.M = h.nocc;
+      s.N = h.Np;
+      s.ldc = h.Np;
+      s.epi = 1;
+      s.base = it.Cd;
+      s.ldb = h.Np;
+      s.coef = make_double2(0.0, j == m ? 2.0 * theta : theta);
+      s.C = (j == m) ? it.Cd : it.Y[j & 1];
+      gs[j - 1][i] = s;
+    }
+    CnCheckItem c{};
+    c.a = it.Y[(m - 1) & 1];
+    c.b = it.Y[(m - 2) & 1];
+    c.rows = h.nocc;
+    c.cols = h.N;
+    c.ld = h.Np;
+    c.traj = it.traj;
+    ck[i] = c;
+  }
+  TRY(upload(ctx, &ctx->d_gD, gD.data(), gD.size()));
+  TRY(upload(ctx, &ctx->d_gM, gM.data(), gM.size()));
+  ctx->sweep.assign(m, nullptr);
+  for (int j = 0; j < m; ++j) TRY(upload(ctx, &ctx->sweep[j], gs[j].data(), gs[j].size()));
+  // the last two iterates are compared once there are two of them (m >= 3)
+  if (m >= 3) TRY(upload(ctx, &ctx->d_cnchk, ck.data(), ck.size()));
+  return VGTB_OK;
+}
+
+// Crank-Nicolson step (Eq. 5) for every trajectory and k:
+//   D = 2 C C^dagger -> observables and SCC shift at t_n -> H(t_{n+1/2}) ->
+//   M = S^-1 H -> fixed-point sweeps Y^dagger <- C^dagger + i (dt/2) Y^dagger M^dagger
+//   (Y = (1 + i (dt/2) M)^-1 C) -> C^dagger(t_{n+1}) = 2 Y^dagger - C^dagger, fused
+//   into the last sweep -> convergence check -> step counter.
+// Event classes: obs (density product + sums), scc, phase, gemm1 (M), gemm2
+// (sweeps), leap (check + counter).
+int enqueue_step_cn(vgtb_ctx* ctx, cudaEvent_t* ev, unsigned evflag) {
+  cudaStream_t st = ctx->stream;
+  const int nt = (int)ctx->trj.size();
+  const int stride = ctx->opt.obs_stride > 0 ? ctx->opt.obs_stride : 1;
+  launch_gemm_f64(ctx->d_gD, ctx->n_items, ctx->max_Np, ctx->max_Np, nullptr, st);
+  launch_obs(ctx->d_sys, ctx->d_trj, ctx->d_items, ctx->d_wpre, nt, ctx->total_warps, ctx->d_step, 0, -1, st);
+  if (ev) CK(cudaEventRecordWithFlags(ev[1], st, evflag));
+  launch_scc(ctx->d_sys, ctx->d_trj, nt, ctx->d_step, stride, -1, 1, ctx->max_nat, st);
+  if (ev) CK(cudaEventRecordWithFlags(ev[2], st, evflag));
+  launch_phase(ctx->d_sys, ctx->d_trj, ctx->d_items, ctx->d_wpre, nt, ctx->total_warps, ctx->d_step, PH_FP64_CN, -1,
+               st);
+  if (ev) CK(cudaEventRecordWithFlags(ev[3], st, evflag));
+  launch_gemm_f64(ctx->d_gM, ctx->n_items, ctx->max_Np, ctx->max_Np, nullptr, st);
+  if (ev) CK(cudaEventRecordWithFlags(ev[4], st, evflag));
+  for (GemmF64Item* g : ctx->sweep) launch_gemm_f64(g, ctx->n_items, ctx->max_nocc, ctx->max_Np, nullptr, st);
+  if (ev) CK(cudaEventRecordWithFlags(ev[5], st, evflag));
+  if (ctx->d_cnchk)
+    launch_cn_check(ctx->d_cnchk, ctx->n_items, ctx->max_nocc * ctx->max_Np, ctx->d_trj, ctx->opt.cn_tol, st);
+  launch_increment(ctx->d_step, st);
+  if (ev) CK(cudaEventRecordWithFlags(ev[6], st, evflag));
+  CK(cudaGetLastError());
+  return VGTB_OK;
+}
+
+int obs_mode(const vgtb_ctx* ctx) { return ctx->split ? 2 : (ctx->delta ? 1 : 0); }
+
 int enqueue_step(vgtb_ctx* ctx, cudaEvent_t* ev) {
   cudaStream_t st = ctx->stream;
   unsigned evflag = cudaEventRecordDefault;
@@ -743,7 +872,8 @@ int enqueue_step(vgtb_ctx* ctx, cudaEvent_t* ev) {
   const int nt = (int)ctx->trj.size();
   const int stride = ctx->opt.obs_stride > 0 ? ctx->opt.obs_stride : 1;
   if (ev) CK(cudaEventRecordWithFlags(ev[0], st, evflag));
-  launch_obs(ctx->d_sys, ctx->d_trj, ctx->d_items, ctx->d_wpre, nt, ctx->total_warps, ctx->d_step, ctx->delta ? 1 : 0,
+  if (ctx->cn) return enqueue_step_cn(ctx, ev, evflag);
+  launch_obs(ctx->d_sys, ctx->d_trj, ctx->d_items, ctx->d_wpre, nt, ctx->total_warps, ctx->d_step, obs_mode(ctx),
              -1, st);
   if (ev) CK(cudaEventRecordWithFlags(ev[1], st, evflag));
   launch_scc(ctx->d_sys, ctx->d_trj, nt, ctx->d_step, stride, -1, 1, ctx->max_nat, st);
@@ -825,9 +955,14 @@ int check_status(vgtb_ctx* ctx) {
     CK(cudaMemcpyAsync(&st, ctx->trj[t].status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     if (st & ST_TIMEOUT) return fail(ctx, VGTB_E_TIMEOUT, "trajectory %zu: a bounded device wait expired", t);
+    // an unconverged Crank-Nicolson solve is the cause of any drift that follows it
+    if (st & ST_CN_NOCONV)
+      return fail(ctx, VGTB_E_UNSTABLE,
+                  "trajectory %zu: Crank-Nicolson fixed point not converged (raise cn_iter or lower dt)", t);
     if (st & ST_NONFINITE) return fail(ctx, VGTB_E_UNSTABLE, "trajectory %zu: non-finite observables", t);
     if (st & ST_DRIFT) return fail(ctx, VGTB_E_UNSTABLE, "trajectory %zu: electron count drifted", t);
   }
+  if (!ctx->split) return VGTB_OK;
   const int tc = tc_status(ctx->tc1, ctx->stream) | tc_status(ctx->tc2, ctx->stream);
   if (tc) return fail(ctx, VGTB_E_TIMEOUT, "tcgen05 product reported status %d (bounded wait expired)", tc);
   return VGTB_OK;
@@ -850,6 +985,9 @@ void vgtb_default_options(vgtb_options* opt) {
   opt->timeout_ns = 2000000000LL;
   opt->scc_tol = 1e-11;
   opt->scc_max_iter = 200;
+  opt->integrator = VGTB_LEAPFROG;
+  opt->cn_iter = 12;
+  opt->cn_tol = 1e-10;
 }
 
 int vgtb_create(vgtb_ctx** out, const vgtb_system* sys, const vgtb_options* opt) {
@@ -877,8 +1015,17 @@ int vgtb_create_batch(vgtb_ctx** out, int n_sys, const vgtb_system* sys, int n_t
     return bail(fail(ctx, VGTB_E_INVALID, "unknown precision %d", ctx->opt.precision));
   if (ctx->opt.init != VGTB_INIT_GROUND && ctx->opt.init != VGTB_INIT_USER)
     return bail(fail(ctx, VGTB_E_INVALID, "unknown init %d", ctx->opt.init));
+  if (ctx->opt.integrator != VGTB_LEAPFROG && ctx->opt.integrator != VGTB_CRANK_NICOLSON)
+    return bail(fail(ctx, VGTB_E_INVALID, "unknown integrator %d", ctx->opt.integrator));
   ctx->split = ctx->opt.precision == VGTB_SPLIT_BF16X3;
-  ctx->delta = ctx->split || ctx->opt.delta_form != 0;
+  ctx->cn = ctx->opt.integrator == VGTB_CRANK_NICOLSON;
+  if (ctx->cn && ctx->split)
+    return bail(fail(ctx, VGTB_E_UNSUPPORTED, "the Crank-Nicolson integrator runs in FP64 precision only"));
+  if (ctx->opt.cn_iter <= 0) ctx->opt.cn_iter = 12;
+  if (ctx->opt.cn_iter < 2)
+    return bail(fail(ctx, VGTB_E_INVALID, "cn_iter must be >= 2 (the last sweep writes C in place)"));
+  if (!(ctx->opt.cn_tol > 0.0)) ctx->opt.cn_tol = 1e-10;
+  ctx->delta = ctx->split || (ctx->opt.delta_form != 0 && !ctx->cn);
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return bail(fail(ctx, VGTB_E_CUDA, "no CUDA device"));
   if (ctx->split && !tc_gemm_supported())
@@ -903,8 +1050,9 @@ int vgtb_create_batch(vgtb_ctx** out, int n_sys, const vgtb_system* sys, int n_t
   std::vector<DevSys> dsys(n_sys);
   int rc;
   for (int s = 0; s < n_sys; ++s) {
-    rc = prepare_system(ctx, s, sys[s], ctx->sys[s], dsys[s], ctx->opt.init == VGTB_INIT_GROUND);
+    rc = prepare_system(ctx, s, sys[s], ctx->sys[s], dsys[s], ctx->opt.init == VGTB_INIT_GROUND || ctx->cn);
     if (rc) return bail(rc);
+    ctx->max_nocc = std::max(ctx->max_nocc, ctx->sys[s].nocc);
     ctx->max_nat = std::max(ctx->max_nat, ctx->sys[s].nat);
     ctx->max_Np = std::max(ctx->max_Np, ctx->sys[s].Np);
   }
@@ -947,9 +1095,10 @@ int vgtb_create_batch(vgtb_ctx** out, int n_sys, const vgtb_system* sys, int n_t
       it.traj = t;
       it.k = k;
       double2* lv = nullptr;
-      if ((rc = dalloc(ctx, &lv, 2 * NN))) return bail(rc);
+      // Crank-Nicolson rebuilds D from C at every level: one buffer serves both parities
+      if ((rc = dalloc(ctx, &lv, ctx->cn ? NN : 2 * NN))) return bail(rc);
       it.D[0] = lv;
-      it.D[1] = lv + NN;
+      it.D[1] = ctx->cn ? lv : lv + NN;
       if (ctx->split) {
         const size_t li = sys_next[T.sys]++;
         it.dD_p = fam[T.sys].dD + 4 * NN * li;
@@ -957,6 +1106,13 @@ int vgtb_create_batch(vgtb_ctx** out, int n_sys, const vgtb_system* sys, int n_t
         it.dHemb_p = fam[T.sys].dHemb + 8 * NN * li;
         it.Wemb_p = fam[T.sys].Wemb + 8 * NN * li;
         it.Xf = fam[T.sys].Xf + 2 * NN * li;
+      } else if (ctx->cn) {
+        const size_t nc = (size_t)h.nocc * h.Np;
+        if ((rc = dalloc(ctx, &it.H, NN))) return bail(rc);
+        if ((rc = dalloc(ctx, &it.W, NN))) return bail(rc);
+        if ((rc = dalloc(ctx, &it.Cd, nc))) return bail(rc);
+        if ((rc = dalloc(ctx, &it.Y[0], nc))) return bail(rc);
+        if ((rc = dalloc(ctx, &it.Y[1], nc))) return bail(rc);
       } else {
         if ((rc = dalloc(ctx, &it.H, NN))) return bail(rc);
         if ((rc = dalloc(ctx, &it.W, NN))) return bail(rc);
@@ -967,6 +1123,7 @@ int vgtb_create_batch(vgtb_ctx** out, int n_sys, const vgtb_system* sys, int n_t
     }
     if ((rc = dalloc(ctx, &T.dq, h.nat))) return bail(rc);
     if ((rc = dalloc(ctx, &T.eps, h.nat))) return bail(rc);
+    if (ctx->cn && (rc = dalloc(ctx, &T.eps_lv, 2 * (size_t)h.nat))) return bail(rc);
     if ((rc = dalloc(ctx, &T.part, 5 * (size_t)h.n_tgt))) return bail(rc);
     if ((rc = dalloc(ctx, &T.erow, h.nat))) return bail(rc);
     if ((rc = dalloc(ctx, &T.apart, 4 * (size_t)h.nat))) return bail(rc);
@@ -1024,7 +1181,9 @@ int vgtb_create_batch(vgtb_ctx** out, int n_sys, const vgtb_system* sys, int n_t
     l.mode = 0;
     lv[i] = l;
   }
-  if (!ctx->split) {
+  if (ctx->cn) {
+    if ((rc = build_cn_lists(ctx))) return bail(rc);
+  } else if (!ctx->split) {
     if ((rc = upload(ctx, &ctx->d_g1, g1.data(), g1.size()))) return bail(rc);
     if ((rc = upload(ctx, &ctx->d_g2, g2.data(), g2.size()))) return bail(rc);
   }
@@ -1066,6 +1225,8 @@ int vgtb_create_batch(vgtb_ctx** out, int n_sys, const vgtb_system* sys, int n_t
 
 int vgtb_set_density(vgtb_ctx* ctx, int s, int k, const double* d0) {
   if (!ctx) return VGTB_E_INVALID;
+  if (ctx->cn)
+    return fail(ctx, VGTB_E_INVALID, "the Crank-Nicolson integrator starts from states: use vgtb_set_coefficients");
   if (s < 0 || s >= (int)ctx->sys.size()) return fail(ctx, VGTB_E_INVALID, "system index %d out of range", s);
   HostSys& h = ctx->sys[s];
   if (k < 0 || k >= h.nk) return fail(ctx, VGTB_E_INVALID, "k index %d out of range", k);
@@ -1083,6 +1244,70 @@ int vgtb_set_density(vgtb_ctx* ctx, int s, int k, const double* d0) {
     TRY(finish_density(ctx, s));
     TRY(reset_all(ctx));
   }
+  return VGTB_OK;
+}
+
+int vgtb_set_coefficients(vgtb_ctx* ctx, int s, int k, int n_occ, const double* c) {
+  if (!ctx) return VGTB_E_INVALID;
+  if (!ctx->cn) return fail(ctx, VGTB_E_INVALID, "vgtb_set_coefficients needs the Crank-Nicolson integrator");
+  if (s < 0 || s >= (int)ctx->sys.size()) return fail(ctx, VGTB_E_INVALID, "system index %d out of range", s);
+  HostSys& h = ctx->sys[s];
+  if (k < 0 || k >= h.nk) return fail(ctx, VGTB_E_INVALID, "k index %d out of range", k);
+  if (n_occ != h.nocc) return fail(ctx, VGTB_E_INVALID, "n_occ = %d, the system has %d occupied states", n_occ, h.nocc);
+  if (!c || !finite_all(c, 2 * (size_t)h.N * h.nocc))
+    return fail(ctx, VGTB_E_INVALID, "coefficients are NULL or non-finite");
+  const size_t NN = (size_t)h.Np * h.Np;
+  double2* tmp = nullptr;
+  CK(cudaMallocAsync(&tmp, sizeof(double2) * (size_t)h.N * h.nocc, ctx->stream));
+  CK(cudaMemcpyAsync(tmp, c, sizeof(double2) * (size_t)h.N * h.nocc, cudaMemcpyHostToDevice, ctx->stream));
+  double2* Cd = h.C0d + (size_t)k * h.nocc * h.Np;
+  launch_conj_transpose(tmp, h.nocc, Cd, h.Np, h.nocc, h.N, ctx->stream);
+  // D_k(0) = 2 C C^dagger (charges of the start, vgtb_get_initial_density)
+  GemmF64Item g{};
+  g.A[0] = g.R[0] = Cd;
+  g.K[0] = h.nocc;
+  g.lda[0] = g.ldr[0] = h.Np;
+  g.nseg = 1;
+  g.conj_t = 3;
+  g.M = g.N = h.N;
+  g.ldc = h.Np;
+  g.C = h.D0 + k * NN;
+  g.epi = 1;
+  g.coef = make_double2(2.0, 0.0);
+  GemmF64Item* dg = nullptr;
+  CK(cudaMallocAsync(&dg, sizeof(g), ctx->stream));
+  CK(cudaMemcpyAsync(dg, &g, sizeof(g), cudaMemcpyHostToDevice, ctx->stream));
+  launch_gemm_f64(dg, 1, h.N, h.N, nullptr, ctx->stream);
+  CK(cudaGetLastError());
+  CK(cudaFreeAsync(tmp, ctx->stream));
+  CK(cudaFreeAsync(dg, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  h.k_set.resize(h.nk, 0);
+  h.k_set[k] = 1;
+  bool all = true;
+  for (char x : h.k_set) all &= x != 0;
+  if (all || h.density_set) {
+    TRY(finish_density(ctx, s));
+    TRY(reset_all(ctx));
+  }
+  return VGTB_OK;
+}
+
+int vgtb_get_coefficients(vgtb_ctx* ctx, int t, int k, double* c_out) {
+  if (!ctx) return VGTB_E_INVALID;
+  if (!ctx->cn) return fail(ctx, VGTB_E_INVALID, "vgtb_get_coefficients needs the Crank-Nicolson integrator");
+  if (t < 0 || t >= (int)ctx->trj.size()) return fail(ctx, VGTB_E_INVALID, "trajectory %d out of range", t);
+  const HostTraj& T = ctx->trj[t];
+  const HostSys& h = ctx->sys[T.sys];
+  if (k < 0 || k >= h.nk || !c_out) return fail(ctx, VGTB_E_INVALID, "bad k or NULL output");
+  const DevItem& it = ctx->items_h[T.item0 + k];
+  double2* tmp = nullptr;
+  CK(cudaMallocAsync(&tmp, sizeof(double2) * (size_t)h.N * h.nocc, ctx->stream));
+  launch_conj_transpose(it.Cd, h.Np, tmp, h.nocc, h.N, h.nocc, ctx->stream);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(c_out, tmp, sizeof(double2) * (size_t)h.N * h.nocc, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaFreeAsync(tmp, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
   return VGTB_OK;
 }
 
@@ -1134,7 +1359,8 @@ int vgtb_propagate(vgtb_ctx* ctx, int nsteps) {
   }
   // observables of the final level
   const int nt = (int)ctx->trj.size();
-  launch_obs(ctx->d_sys, ctx->d_trj, ctx->d_items, ctx->d_wpre, nt, ctx->total_warps, ctx->d_step, ctx->delta ? 1 : 0,
+  if (ctx->cn) launch_gemm_f64(ctx->d_gD, ctx->n_items, ctx->max_Np, ctx->max_Np, nullptr, ctx->stream);
+  launch_obs(ctx->d_sys, ctx->d_trj, ctx->d_items, ctx->d_wpre, nt, ctx->total_warps, ctx->d_step, obs_mode(ctx),
              -1, ctx->stream);
   launch_scc(ctx->d_sys, ctx->d_trj, nt, ctx->d_step, ctx->opt.obs_stride, -1, 1, ctx->max_nat, ctx->stream);
   CK(cudaGetLastError());
@@ -1255,15 +1481,24 @@ int vgtb_get_initial_density(vgtb_ctx* ctx, int s, int k, double* d_out) {
   return VGTB_OK;
 }
 
+// State layout: 4 header words (tag, n, items, form), then per item the two
+// leapfrog levels (2 Np^2 complex), or for Crank-Nicolson per item C^dagger
+// (nocc x Np complex) followed by the two latest SCC shifts of every
+// trajectory (2 nat doubles).
 long long vgtb_state_size(const vgtb_ctx* ctx) {
   if (!ctx) return -1;
   long long b = 4 * sizeof(long long);
   for (auto& it : ctx->items_h) {
     const HostSys& h = ctx->sys[it.sys];
-    b += 2LL * h.Np * h.Np * (long long)sizeof(double2);
+    b += ctx->cn ? (long long)h.nocc * h.Np * (long long)sizeof(double2)
+                 : 2LL * h.Np * h.Np * (long long)sizeof(double2);
   }
+  if (ctx->cn)
+    for (auto& t : ctx->trj) b += 2LL * ctx->sys[t.sys].nat * (long long)sizeof(double);
   return b;
 }
+
+static long long state_form(const vgtb_ctx* ctx) { return ctx->cn ? 2 : (ctx->delta ? 1 : 0); }
 
 int vgtb_get_state(vgtb_ctx* ctx, void* buf, long long bytes) {
   if (!ctx || !buf) return VGTB_E_INVALID;
@@ -1272,14 +1507,21 @@ int vgtb_get_state(vgtb_ctx* ctx, void* buf, long long bytes) {
   hd[0] = 0x7674627374617465LL;  // tag
   hd[1] = ctx->n_done;
   hd[2] = ctx->n_items;
-  hd[3] = ctx->delta ? 1 : 0;
+  hd[3] = state_form(ctx);
   char* p = (char*)buf + 4 * sizeof(long long);
   for (auto& it : ctx->items_h) {
     const HostSys& h = ctx->sys[it.sys];
-    const size_t NN = (size_t)h.Np * h.Np;
-    CK(cudaMemcpyAsync(p, it.D[0], 2 * NN * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream));
-    p += 2 * NN * sizeof(double2);
+    const size_t bytes_it = ctx->cn ? (size_t)h.nocc * h.Np * sizeof(double2) : 2 * (size_t)h.Np * h.Np * sizeof(double2);
+    CK(cudaMemcpyAsync(p, ctx->cn ? (const void*)it.Cd : (const void*)it.D[0], bytes_it, cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    p += bytes_it;
   }
+  if (ctx->cn)
+    for (auto& t : ctx->trj) {
+      const size_t b = 2 * (size_t)ctx->sys[t.sys].nat * sizeof(double);
+      CK(cudaMemcpyAsync(p, t.eps_lv, b, cudaMemcpyDeviceToHost, ctx->stream));
+      p += b;
+    }
   CK(cudaStreamSynchronize(ctx->stream));
   return VGTB_OK;
 }
@@ -1288,7 +1530,7 @@ int vgtb_set_state(vgtb_ctx* ctx, const void* buf, long long bytes) {
   if (!ctx || !buf) return VGTB_E_INVALID;
   if (bytes < vgtb_state_size(ctx)) return fail(ctx, VGTB_E_INVALID, "state buffer too small");
   const long long* hd = (const long long*)buf;
-  if (hd[0] != 0x7674627374617465LL || hd[2] != ctx->n_items || hd[3] != (ctx->delta ? 1 : 0))
+  if (hd[0] != 0x7674627374617465LL || hd[2] != ctx->n_items || hd[3] != state_form(ctx))
     return fail(ctx, VGTB_E_INVALID, "state does not belong to a context of this shape");
   const int n = (int)hd[1];
   for (auto& t : ctx->trj)
@@ -1297,10 +1539,21 @@ int vgtb_set_state(vgtb_ctx* ctx, const void* buf, long long bytes) {
   for (auto& it : ctx->items_h) {
     const HostSys& h = ctx->sys[it.sys];
     const size_t NN = (size_t)h.Np * h.Np;
+    if (ctx->cn) {
+      CK(cudaMemcpyAsync(it.Cd, p, (size_t)h.nocc * h.Np * sizeof(double2), cudaMemcpyHostToDevice, ctx->stream));
+      p += (size_t)h.nocc * h.Np * sizeof(double2);
+      continue;
+    }
     CK(cudaMemcpyAsync(it.D[0], p, 2 * NN * sizeof(double2), cudaMemcpyHostToDevice, ctx->stream));
     if (it.dD_p) launch_split_planar(it.D[n & 1], it.dD_p, h.N, h.Np, ctx->stream);
     p += 2 * NN * sizeof(double2);
   }
+  if (ctx->cn)
+    for (auto& t : ctx->trj) {
+      const size_t b = 2 * (size_t)ctx->sys[t.sys].nat * sizeof(double);
+      CK(cudaMemcpyAsync(t.eps_lv, p, b, cudaMemcpyHostToDevice, ctx->stream));
+      p += b;
+    }
   CK(cudaMemcpyAsync(ctx->d_step, &n, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaMemsetAsync(ctx->d_counter, 0, sizeof(int), ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));

@@ -26,7 +26,40 @@ enum : int {
   ST_DRIFT = 2,          // electron count drifted
   ST_TIMEOUT = 4,        // a bounded device wait gave up
   ST_BADSHAPE = 8,       // a kernel saw an impossible shape
+  ST_CN_NOCONV = 16,     // Crank-Nicolson fixed point still moving after the last sweep
 };
+
+// ---------------------------------------------------------------------------
+// IEEE-754 float <-> double conversions done with integer bit operations.
+// GB300 runs FP64 instructions, conversions included, at a small fraction of
+// the integer rate, so the split-form kernels convert with these and keep the
+// FP64 pipe for the arithmetic that needs it.  float -> double is exact (signed zero for float zeros and
+// subnormals, which are below 1.2e-38); double -> float rounds to nearest even
+// and flushes magnitudes below 2^-126 to signed zero and above the float range
+// to infinity.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double f2d_bits(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t e = (u >> 23) & 0xffu;
+  const uint32_t sign = u & 0x80000000u;
+  const uint32_t ee = (e == 255u) ? 2047u : e + 896u;  // exponent bias 1023 - 127
+  const uint32_t hi = (e == 0u) ? sign : (sign | (ee << 20) | ((u >> 3) & 0xfffffu));
+  const uint32_t lo = (e == 0u) ? 0u : (u << 29);
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+__device__ __forceinline__ float d2f_bits(double d) {
+  const uint32_t hi = (uint32_t)__double2hiint(d), lo = (uint32_t)__double2loint(d);
+  const uint32_t sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
+  const uint32_t mant = ((hi & 0xfffffu) << 3) | (lo >> 29);
+  const uint32_t rest = lo & 0x1fffffffu;
+  uint32_t f = sign | ((uint32_t)e << 23) | mant;
+  f += (rest > 0x10000000u || (rest == 0x10000000u && (mant & 1u))) ? 1u : 0u;
+  f = (e <= 0) ? sign : f;
+  f = (e >= 255) ? (sign | 0x7f800000u) : f;
+  return __uint_as_float(f);
+}
 
 struct DevSys {
   int N, Np, nat, nk, n_tgt, n_blk;
@@ -66,6 +99,8 @@ struct DevSys {
   const float* dsf;        // [3][ds_stride]
   const float2* phasef;    // [nk][n_blk]
   float* R0f;              // [nk][Np][2Np] planar
+  float4* kf;              // [nk][n_el][3] FP32 k-space blocks {S, P_x}, {P_y, P_z}, {H0, 0} (split form)
+  const float* wkf;        // [nk] k weights as float (split form)
 };
 
 struct DevTraj {
@@ -79,6 +114,7 @@ struct DevTraj {
   double* q;               // [(n_times-1)/stride+1][nat]
   double* dq;              // [nat] current dq
   double* eps;             // [nat] current eps
+  double* eps_lv;          // [2][nat] eps of the two latest levels by parity (Crank-Nicolson), or null
   double* part;            // [n_tgt][5] per-target partial sums
   double* erow;            // [nat] dq_I eps_I (energy of the SCC term, per row)
   double* apart;           // [nat][4] per-atom shares of T_x, T_y, T_z and the band energy
@@ -98,17 +134,34 @@ struct DevItem {
   __nv_bfloat16* dHemb_p;  // split form: [2][2Np][2Np] embedded dH
   __nv_bfloat16* Wemb_p;   // split form: [2][2Np][2Np] embedded W
   float* Xf;               // split form: [Np][2Np] planar X
+  double2* Cd;             // Crank-Nicolson: occupied states as rows, C^dagger [nocc][Np]
+  double2* Y[2];           // Crank-Nicolson: fixed-point iterates [nocc][Np]
 };
+
+// Crank-Nicolson convergence check of one item: max |Y[a] - Y[b]| over nocc x N
+struct CnCheckItem {
+  const double2* a;
+  const double2* b;
+  int rows, cols, ld, traj;
+};
+void launch_cn_check(const CnCheckItem* items, int n_items, int max_elems, const DevTraj* trj, double tol,
+                     cudaStream_t st);
+// dst[r][c] = conj(src[c][r]) for r < rows, c < cols (dst row stride ldd, src row stride lds)
+void launch_conj_transpose(const double2* src, int lds, double2* dst, int ldd, int rows, int cols, cudaStream_t st);
 
 // What the phase-build kernel writes.
 enum PhaseMode : int {
   PH_FP64_PLAIN = 0,   // H = H0 + (alpha + (eps_I+eps_J)/2) S + (i/c) A.dS  -> item.H
   PH_FP64_DELTA = 1,   // H without alpha -> item.H ; dH = ((deps_I+deps_J)/2) S + (i/c) A.dS -> item.dH
+  PH_FP64_CN = 2,      // H at t_{n+1/2} without alpha: midpoint A, extrapolated eps -> item.H
 };
 
 // Launchers (all enqueue on `st`)
+// delta: 0 = D itself (FP64), 1 = dD with the D0 part from obs0 (FP64), 2 = the same
+// with the dD sums in FP32 (split form)
 void launch_obs(const DevSys* sys, const DevTraj* trj, const DevItem* items, const int* warp_prefix,
                 int n_traj, int total_warps, const int* step, int delta, int fixed_step, cudaStream_t st);
+void launch_kblocks_f32(const DevSys* sys, int s_idx, long long n, cudaStream_t st);
 void launch_scc(const DevSys* sys, DevTraj* trj, int n_traj, const int* step, int stride,
                 int fixed_step, int record, int max_nat, cudaStream_t st);
 void launch_phase_split(const DevSys* sys, const DevTraj* trj, const DevItem* items, const int* warp_prefix,
@@ -132,6 +185,11 @@ struct GemmF64Item {
   int K[2];
   int lda[2], ldr[2];
   int nseg, M, N, ldc;
+  int conj_t;              // bit 0: A(m, k) = conj(A[k * lda + m]); bit 1: the same for R
+  int epi;                 // 0: C = acc;  1: C = coef * acc (+ base when base != null)
+  double2 coef;
+  const double2* base;     // may alias C (element-wise read-before-write by one thread)
+  int ldb;
 };
 void launch_gemm_f64(const GemmF64Item* items, int n_items, int max_m, int max_n, const int* step,
                      cudaStream_t st);

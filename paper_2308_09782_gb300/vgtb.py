@@ -23,13 +23,16 @@ FP64 = 0
 SPLIT_BF16X3 = 1
 INIT_GROUND = 0
 INIT_USER = 1
+LEAPFROG = 0
+CRANK_NICOLSON = 1
 KERNEL_CLASSES = ["obs", "scc", "phase", "gemm1", "gemm2", "leap"]
 
 EXPORTS = ["vgtb_default_options", "vgtb_create", "vgtb_create_batch", "vgtb_set_density",
            "vgtb_set_field", "vgtb_propagate", "vgtb_steps_done", "vgtb_observables",
            "vgtb_get_density", "vgtb_get_initial_density", "vgtb_state_size", "vgtb_get_state", "vgtb_set_state",
            "vgtb_profile", "vgtb_kernel_stats", "vgtb_last_error", "vgtb_destroy",
-           "vgtb_diag_split_chain", "vgtb_split_cgemm_noalloc", "vgtb_spectrum", "vgtb_group_charges"]
+           "vgtb_diag_split_chain", "vgtb_split_cgemm_noalloc", "vgtb_spectrum", "vgtb_group_charges",
+           "vgtb_set_coefficients", "vgtb_get_coefficients"]
 
 
 class VgtbSystem(C.Structure):
@@ -46,7 +49,8 @@ class VgtbOptions(C.Structure):
     _fields_ = [("precision", C.c_int), ("delta_form", C.c_int), ("init", C.c_int),
                 ("cuda_stream", C.c_void_p), ("timeout_ns", C.c_longlong),
                 ("obs_stride", C.c_int), ("graph_steps", C.c_int), ("autotune", C.c_int),
-                ("scc_tol", C.c_double), ("scc_max_iter", C.c_int)]
+                ("scc_tol", C.c_double), ("scc_max_iter", C.c_int),
+                ("integrator", C.c_int), ("cn_iter", C.c_int), ("cn_tol", C.c_double)]
 
 
 _lib = None
@@ -88,6 +92,8 @@ def load(path: str = LIB_PATH):
     lib.vgtb_split_cgemm_noalloc.argtypes = [I, V, V, V, V]
     lib.vgtb_spectrum.argtypes = [ctxp, I, I, I, D, D, I, P(D), P(D), P(D)]
     lib.vgtb_group_charges.argtypes = [ctxp, I, I, P(I), P(D)]
+    lib.vgtb_set_coefficients.argtypes = [ctxp, I, I, I, P(D)]
+    lib.vgtb_get_coefficients.argtypes = [ctxp, I, I, P(D)]
     for name in EXPORTS:
         if name not in ("vgtb_default_options", "vgtb_last_error", "vgtb_destroy", "vgtb_state_size"):
             getattr(lib, name).restype = I
@@ -200,6 +206,19 @@ class Context:
     def set_density(self, sys_index: int, k: int, d0):
         d = np.ascontiguousarray(d0, np.complex128)
         self._check(load().vgtb_set_density(self._h, sys_index, k, d.ctypes.data_as(C.POINTER(C.c_double))))
+
+    def set_coefficients(self, sys_index: int, k: int, c):
+        """Crank-Nicolson start: occupied states C_k(0), shape [N, n_occ] (column n = state n)."""
+        a = np.ascontiguousarray(c, np.complex128)
+        self._check(load().vgtb_set_coefficients(self._h, sys_index, k, a.shape[1],
+                                                 a.ctypes.data_as(C.POINTER(C.c_double))))
+
+    def get_coefficients(self, traj: int, k: int, n_occ: int):
+        """Crank-Nicolson: C_k(t_n) of trajectory `traj`, shape [N, n_occ]."""
+        s = int(self._traj_sys[traj])
+        out = np.zeros((self.N[s], n_occ), np.complex128)
+        self._check(load().vgtb_get_coefficients(self._h, traj, k, out.ctypes.data_as(C.POINTER(C.c_double))))
+        return out
 
     def set_field(self, traj: int, A):
         a = np.ascontiguousarray(A, np.float64)
