@@ -46,8 +46,13 @@ def parse():
     p.add_argument("--impl", choices=["native", "reference"], default="native")
     p.add_argument("--fp64-steps", type=int, default=20)
     p.add_argument("--cpu-steps", type=int, default=6)
+    p.add_argument("--cn-steps", type=int, default=4,
+                   help="timed steps of the FP64 Crank-Nicolson integrator (0 = skip)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--cpu-1thread-steps", type=int, default=1,
+                   help="oracle steps timed again with one BLAS thread (0 = skip)")
+    p.add_argument("--oracle-probe", type=int, default=0, help=argparse.SUPPRESS)
     p.add_argument("--workload", choices=["si512", "batched"], default="si512",
                    help="si512: the headline; batched: 64/216/512-atom supercells x 8 k x 6 fields in one context")
     return p.parse_args()
@@ -150,6 +155,25 @@ def parse_clock_csv(lines):
 # ---------------------------------------------------------------------------
 # roofline helpers
 # ---------------------------------------------------------------------------
+def fp64_peak_tflops(torch, n=2048, reps=5):
+    """cuBLAS ZGEMM yardstick for the FP64 kernels: best of `reps` complex128
+    n^3 products (8 n^3 flops each) on the current device."""
+    a = torch.randn(n, n, dtype=torch.complex128, device="cuda")
+    b = torch.randn(n, n, dtype=torch.complex128, device="cuda")
+    torch.matmul(a, b)
+    best = 1e30
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    del a, b
+    return 8.0 * n ** 3 / (best * 1e-3) / 1e12
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -174,27 +198,50 @@ def kernel_traffic(kernel: str, per_launch_units: float):
 # ---------------------------------------------------------------------------
 # CPU oracle baseline (bounded sample)
 # ---------------------------------------------------------------------------
-def cpu_baseline(nsteps: int, sysd=None, A=None):
+def cpu_baseline(nsteps: int, sysd=None, A=None, warm_up=True):
     import oracle as O
     from paper_2308_09782_gb300 import inputs
     if sysd is None:
         sysd, A, _ = inputs.config(CONFIG)
     t0 = time.perf_counter()
     ctx = O.setup(sysd)
-    nocc = int(round(sysd["n_electrons"] / 2))
-    eps0 = np.zeros(int(sysd["orb_offset"][-1]))
-    D0 = [O.density_from_hamiltonian(O.hamiltonian(H0, S, P, np.zeros(3), eps0), S, nocc)[0]
-          for S, H0, P in zip(ctx["S"], ctx["H0"], ctx["P"])]
+    # a Hermitian start density with Tr(D S) = N_el; a step costs the same for any values
+    n_orb = int(sysd["orb_offset"][-1])
+    D0 = [(float(sysd["n_electrons"]) / n_orb) * Si for Si in ctx["Sinv"]]
     t_setup = time.perf_counter() - t0
-    O.propagate(sysd, A, 1, D0, ctx=ctx)            # warm-up (one step)
+    if warm_up:
+        O.propagate(sysd, A, 1, D0, ctx=ctx)        # warm-up (one step)
     t1 = time.perf_counter()
     O.propagate(sysd, A, nsteps, D0, ctx=ctx)
     dt = time.perf_counter() - t1
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     return {"value": nsteps / dt, "unit": "steps/s", "cores": cores, "kind": "oracle",
-            "sample": f"{nsteps} oracle steps (plus 1 warm-up) of {CONFIG} (N=2048, Gamma) from a non-SCC "
-                      f"start density; numpy complex128, OpenBLAS threads = {cores} cores; "
+            "sample": f"{nsteps} oracle steps{' (plus 1 warm-up)' if warm_up else ''} of {CONFIG} (N=2048, "
+                      f"Gamma) from D0 = (N_el/N) S^-1; numpy complex128, OpenBLAS threads = {cores} cores; "
                       f"setup {t_setup:.1f} s not timed"}
+
+
+def cpu_baseline_1thread(nsteps: int):
+    """The same oracle timing in a child process limited to one BLAS/OpenMP thread."""
+    if nsteps <= 0:
+        return None
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    try:
+        out = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-probe", str(nsteps)],
+                             env=env, capture_output=True, text=True, timeout=900)
+    except subprocess.TimeoutExpired:
+        return None
+    if out.returncode != 0 or not out.stdout.strip():
+        return None
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def with_1thread(cpu: dict, nsteps: int) -> dict:
+    one = cpu_baseline_1thread(nsteps)
+    if one is not None:
+        cpu["value_1thread"] = one["value"]
+        cpu["sample_1thread"] = one["sample"].replace(f"{one['cores']} cores", "1 thread")
+    return cpu
 
 
 # ---------------------------------------------------------------------------
@@ -214,6 +261,8 @@ def native(args):
     ctx = vgtb.Context(sysd, precision=vgtb.SPLIT_BF16X3, init=vgtb.INIT_GROUND,
                        cuda_stream=stream.cuda_stream, graph_steps=50, autotune=1)
     ctx.set_field(0, A[:n_need])
+    tiles = {f"product{p}": ctx.tile_config(p) for p in (1, 2)}
+    tiles["choice"] = "autotuned at create: fastest of the tcgen05 tile variants (median of 9 launches)"
     ctx.profile(True)
     ctx.propagate(W)
     ctx.profile(True)                            # reset the per-kernel counters
@@ -241,6 +290,7 @@ def native(args):
     cf.set_density(0, 0, D0)
     cf.set_field(0, A[:Kf + 3])
     cf.propagate(2)
+    cf.profile(True)
     torch.cuda.synchronize()
     f0 = torch.cuda.Event(enable_timing=True)
     f1 = torch.cuda.Event(enable_timing=True)
@@ -249,8 +299,45 @@ def native(args):
     f1.record(stream)
     torch.cuda.synchronize()
     ms_f = max_over_ranks(f0.elapsed_time(f1))
+    stats_f = cf.kernel_stats()
     J_f, _, _ = cf.observables(0, charges=False)
     cf.close()
+    p64 = fp64_peak_tflops(torch)
+
+    # FP64 Crank-Nicolson integrator (Eq. 5) from the library's ground state
+    cn = None
+    Kc = args.cn_steps
+    if Kc > 0:
+        cc = vgtb.Context(sysd, precision=vgtb.FP64, init=vgtb.INIT_GROUND, integrator=vgtb.CRANK_NICOLSON,
+                          cuda_stream=stream.cuda_stream, graph_steps=1)
+        cc.set_field(0, A[:Kc + 3])
+        cc.propagate(2)
+        cc.profile(True)
+        torch.cuda.synchronize()
+        c0 = torch.cuda.Event(enable_timing=True)
+        c1 = torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        cc.propagate(Kc)
+        c1.record(stream)
+        torch.cuda.synchronize()
+        ms_c = max_over_ranks(c0.elapsed_time(c1))
+        st_c = cc.kernel_stats()
+        sweeps = cc._opt.cn_iter
+        cc.close()
+        nocc = int(round(float(sysd["n_electrons"]) / 2))
+        Nc = int(sysd["orb_offset"][-1])
+        Npc = (Nc + 127) // 128 * 128
+        f_sweep = 8.0 * nocc * Npc * Npc                 # one fixed-point sweep, complex FP64
+        t_sweep = st_c["gemm2"][1] / max(st_c["gemm2"][0], 1) / sweeps
+        a_sweep = f_sweep / (t_sweep * 1e-3) / 1e12
+        cn = {"value": round(world * Kc / (ms_c / 1e3), 4), "unit": "steps/s", "steps": Kc,
+              "ms_per_step": round(ms_c / Kc, 2), "sweeps_per_step": sweeps, "dtype": "f64",
+              "kernel_ms_per_step": {k: round(v[1] / max(v[0], 1), 3) for k, v in st_c.items()},
+              "roofline": {"bound": "fp64", "kernel": "k_gemm_f64 (fixed-point sweep C^dagger + i dt/2 Y^dagger M^dagger)",
+                           "achieved": round(a_sweep, 3), "peak": round(p64, 3), "unit": "TFLOP/s",
+                           "frac": round(a_sweep / p64, 4),
+                           "peak_kind": "cuBLAS ZGEMM 2048^3 measured in this run (torch.matmul complex128)",
+                           "flops_per_launch": f_sweep}}
     nj = min(len(J_f), len(J_split))
     j_err = float(np.linalg.norm(J_split[:nj] - J_f[:nj]) / np.linalg.norm(J_f[:nj]))
 
@@ -293,7 +380,7 @@ def native(args):
     kern_ms = {k: (v[1] / max(v[0], 1)) for k, v in stats.items()}
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(args.cpu_steps)
+        cpu = with_1thread(cpu_baseline(args.cpu_steps), args.cpu_1thread_steps)
     if rank != 0:
         return
     line = {
@@ -301,13 +388,22 @@ def native(args):
         "warmup": W, "ms_per_step": round(step_ms, 4), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16x3 (f32 accumulate) + f64 master", "data": "synthetic",
         "config": {"workload": WORKLOAD, "name": CONFIG, "precision": "split_bf16x3 delta form",
-                   "tiles": "autotuned per product at create (6 tcgen05 variants)",
+                   "tiles": tiles,
                    "parallelism": f"{world} independent replica(s)",
                    "l2": "working set ~0.6 GB per step, larger than the 129 MB L2 (no flush)",
                    "fs_per_hour": round(value / world * 0.2 * AU_FS * 3600, 2)},
         "fp64": {"value": round(world * Kf / (ms_f / 1e3), 3), "unit": "steps/s", "steps": Kf,
                  "ms_per_step": round(ms_f / Kf, 3),
-                 "fs_per_hour": round(Kf / (ms_f / 1e3) * 0.2 * AU_FS * 3600, 3)},
+                 "fs_per_hour": round(Kf / (ms_f / 1e3) * 0.2 * AU_FS * 3600, 3),
+                 "kernel_ms_per_step": {k: round(v[1] / max(v[0], 1), 3) for k, v in stats_f.items()},
+                 "roofline": {"bound": "fp64", "kernel": "k_gemm_f64 (product 1: W = D H)",
+                              "achieved": round(8.0 * Np ** 3 / (stats_f["gemm1"][1] / max(stats_f["gemm1"][0], 1)
+                                                                  * 1e-3) / 1e12, 3),
+                              "peak": round(p64, 3), "unit": "TFLOP/s",
+                              "frac": round(8.0 * Np ** 3 / (stats_f["gemm1"][1] / max(stats_f["gemm1"][0], 1)
+                                                             * 1e-3) / 1e12 / p64, 4),
+                              "peak_kind": "cuBLAS ZGEMM 2048^3 measured in this run (torch.matmul complex128)"}},
+        "crank_nicolson": cn,
         "j_rel_err_split_vs_fp64": j_err, "j_err_steps": nj - 1,
         "roofline": {"bound": "tensor", "kernel": "k_tc_gemm (product 1: W = [dD|D0][H|dH]^dagger)",
                      "achieved": round(ach1, 1), "peak": peak, "unit": "TFLOP/s",
@@ -404,7 +500,7 @@ def reference(args):
     if rank != 0:
         return
     steps = max(1, min(args.steps, 40))
-    cpu = cpu_baseline(steps)
+    cpu = with_1thread(cpu_baseline(steps), args.cpu_1thread_steps)
     v = cpu["value"]
     line = {"metric": METRIC, "value": round(v, 5), "unit": "steps/s", "n_gpus": 0, "steps": steps,
             "warmup": 1, "ms_per_step": round(1e3 / v, 2), "higher_is_better": True, "scaling": "weak",
@@ -417,7 +513,9 @@ def reference(args):
 
 if __name__ == "__main__":
     a = parse()
-    if a.impl == "reference":
+    if a.oracle_probe > 0:
+        print(json.dumps(cpu_baseline(a.oracle_probe, warm_up=False)), flush=True)
+    elif a.impl == "reference":
         reference(a)
     elif a.workload == "batched":
         batched(a)

@@ -225,6 +225,14 @@ int vgtb_kernel_stats(vgtb_ctx* ctx, long long* launches, double* ms, int n);
 
 /* Text of the last error on this context (or of the last failed create when
  * ctx is NULL).  Valid until the next call on the same context. */
+/* Split-precision contexts: the tile variant each tcgen05 product runs with
+ * (product 1 = [dD|D0][H|dH]^dagger, product 2 = S^-1 W^dagger), chosen at
+ * create (variant 0, or the autotuner's fastest).  cfg[4] = {tile width,
+ * pipeline stages, schedule (0 classic, 1 stream-K, 2 whole waves classic and
+ * stream-K over the rest), 1 if the tile spans a 2-SM CTA pair}.
+ * Errors: E_INVALID (product not 1 or 2, NULL), E_STATE (FP64 context). */
+int vgtb_tile_config(const vgtb_ctx* ctx, int product, int* cfg);
+
 const char* vgtb_last_error(const vgtb_ctx* ctx);
 
 /* Release the context and all its device memory.  NULL-safe. */

@@ -20,6 +20,14 @@ extern "C" {
 int vgtb_diag_split_chain(int n, const double* a, const double* r, const double* s, double* w_out,
                           double* x_out);
 
+/* The same with both products forced to tile variant `variant` (0 ..
+ * vgtb_diag_num_variants()-1; -1 = the default), so that every schedule the
+ * autotuner may pick (classic, stream-K, classic waves + stream-K; single CTA
+ * or 2-SM pair) can be checked on its own.  E_INVALID for an index out of range. */
+int vgtb_diag_split_chain_variant(int n, const double* a, const double* r, const double* s, int variant,
+                                  double* w_out, double* x_out);
+int vgtb_diag_num_variants(void);
+
 #ifdef __cplusplus
 }
 #endif

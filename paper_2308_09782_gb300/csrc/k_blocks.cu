@@ -66,6 +66,8 @@ __global__ void __launch_bounds__(256) k_obs(const DevSys* __restrict__ sysv, co
                                              const DevItem* __restrict__ items, const int* __restrict__ wpre,
                                              int n_traj, int total, const int* __restrict__ step, int delta,
                                              int fixed_step) {
+  pdl_wait();
+  pdl_trigger();
   const Unit U = unit_of(wpre, n_traj, total);
   const int lane = threadIdx.x & 15;
   double sS = 0.0, sx = 0.0, sy = 0.0, sz = 0.0, sH = 0.0;
@@ -232,6 +234,8 @@ __global__ void __launch_bounds__(256) k_obs_split(const DevSys* __restrict__ sy
                                                    const DevItem* __restrict__ items, const int* __restrict__ wpre,
                                                    int n_traj, int total, const int* __restrict__ step,
                                                    int fixed_step) {
+  pdl_wait();
+  pdl_trigger();
   const Unit U = unit_of(wpre, n_traj, total);
   const int lane = threadIdx.x & 15;
   float sS = 0.f, sx = 0.f, sy = 0.f, sz = 0.f, sH = 0.f;
@@ -300,9 +304,11 @@ void launch_obs(const DevSys* sys, const DevTraj* trj, const DevItem* items, con
   const int threads = 256;
   const int blocks = (total_units * 16 + threads - 1) / threads;
   if (delta == 2)
-    k_obs_split<<<blocks, threads, 0, st>>>(sys, trj, items, warp_prefix, n_traj, total_units, step, fixed_step);
+    launch_pdl(k_obs_split, blocks, threads, 0, st, sys, trj, items, warp_prefix, n_traj, total_units, step,
+               fixed_step);
   else
-    k_obs<<<blocks, threads, 0, st>>>(sys, trj, items, warp_prefix, n_traj, total_units, step, delta, fixed_step);
+    launch_pdl(k_obs, blocks, threads, 0, st, sys, trj, items, warp_prefix, n_traj, total_units, step, delta,
+               fixed_step);
 }
 
 // Setup (split form): packed FP32 copies of the k-space blocks for k_obs_split.
@@ -337,6 +343,8 @@ constexpr int kAtomsPerCta = kSccThreads / 32;
 __global__ void __launch_bounds__(kSccThreads) k_scc_atoms(const DevSys* __restrict__ sysv, DevTraj* trj, int n_traj,
                                                           int nblk, const int* __restrict__ step, int stride,
                                                           int fixed_step, int record) {
+  pdl_wait();
+  pdl_trigger();
   const int t = blockIdx.x / nblk, b = blockIdx.x % nblk;
   if (t >= n_traj) return;
   DevTraj& T = trj[t];
@@ -366,6 +374,8 @@ __global__ void __launch_bounds__(kSccThreads) k_scc_atoms(const DevSys* __restr
 __global__ void __launch_bounds__(kSccThreads) k_scc_eps(const DevSys* __restrict__ sysv, DevTraj* trj, int n_traj,
                                                         int nblk, const int* __restrict__ step, int fixed_step,
                                                         int record) {
+  pdl_wait();
+  pdl_trigger();
   constexpr int NW = kSccThreads / 32;
   __shared__ double red[6][NW];
   __shared__ int s_last;
@@ -455,9 +465,10 @@ int scc_configure(int max_nat) {
 void launch_scc(const DevSys* sys, DevTraj* trj, int n_traj, const int* step, int stride, int fixed_step,
                 int record, int max_nat, cudaStream_t st) {
   const int nblk_a = (max_nat + kAtomsPerCta - 1) / kAtomsPerCta;
-  k_scc_atoms<<<n_traj * nblk_a, kSccThreads, 0, st>>>(sys, trj, n_traj, nblk_a, step, stride, fixed_step, record);
+  launch_pdl(k_scc_atoms, n_traj * nblk_a, kSccThreads, 0, st, sys, trj, n_traj, nblk_a, step, stride, fixed_step,
+             record);
   const int nblk = (max_nat + kSccRows - 1) / kSccRows;
-  k_scc_eps<<<n_traj * nblk, kSccThreads, 0, st>>>(sys, trj, n_traj, nblk, step, fixed_step, record);
+  launch_pdl(k_scc_eps, n_traj * nblk, kSccThreads, 0, st, sys, trj, n_traj, nblk, step, fixed_step, record);
 }
 
 // ---------------------------------------------------------------------------
@@ -473,6 +484,8 @@ __global__ void __launch_bounds__(256) k_phase(const DevSys* __restrict__ sysv, 
                                                const DevItem* __restrict__ items, const int* __restrict__ wpre,
                                                int n_traj, int total, const int* __restrict__ step, int mode,
                                                int fixed_step) {
+  pdl_wait();
+  pdl_trigger();
   const Unit U = unit_of(wpre, n_traj, total);
   if (!U.active) return;
   const int lane = threadIdx.x & 15;
@@ -535,7 +548,8 @@ void launch_phase(const DevSys* sys, const DevTraj* trj, const DevItem* items, c
                   int n_traj, int total_units, const int* step, int mode, int fixed_step, cudaStream_t st) {
   const int threads = 256;
   const int blocks = (total_units * 16 + threads - 1) / threads;
-  k_phase<<<blocks, threads, 0, st>>>(sys, trj, items, warp_prefix, n_traj, total_units, step, mode, fixed_step);
+  launch_pdl(k_phase, blocks, threads, 0, st, sys, trj, items, warp_prefix, n_traj, total_units, step, mode,
+             fixed_step);
 }
 
 // ---------------------------------------------------------------------------
@@ -568,6 +582,8 @@ __global__ void __launch_bounds__(256) k_phase_split(const DevSys* __restrict__ 
                                                      const DevItem* __restrict__ items,
                                                      const int* __restrict__ wpre, int n_traj, int total,
                                                      const int* __restrict__ step) {
+  pdl_wait();
+  pdl_trigger();
   const Unit U = unit_of(wpre, n_traj, total);
   if (!U.active) return;
   const int lane = threadIdx.x & 15;
@@ -615,7 +631,7 @@ void launch_phase_split(const DevSys* sys, const DevTraj* trj, const DevItem* it
                         int n_traj, int total_units, const int* step, cudaStream_t st) {
   const int threads = 256;
   const int blocks = (total_units * 16 + threads - 1) / threads;
-  k_phase_split<<<blocks, threads, 0, st>>>(sys, trj, items, warp_prefix, n_traj, total_units, step);
+  launch_pdl(k_phase_split, blocks, threads, 0, st, sys, trj, items, warp_prefix, n_traj, total_units, step);
 }
 
 // ---------------------------------------------------------------------------

@@ -22,6 +22,8 @@ constexpr int GT = 64, GK = 16;
 
 __global__ void __launch_bounds__(256) k_gemm_f64(const GemmF64Item* __restrict__ items,
                                                   const int* __restrict__ step) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ double2 As[GK][GT + 1];
   __shared__ double2 Rs[GK][GT + 1];
   const GemmF64Item& it = items[blockIdx.z];
@@ -111,7 +113,7 @@ __global__ void __launch_bounds__(256) k_gemm_f64(const GemmF64Item* __restrict_
 void launch_gemm_f64(const GemmF64Item* items, int n_items, int max_m, int max_n, const int* step,
                      cudaStream_t st) {
   dim3 grid((max_n + GT - 1) / GT, (max_m + GT - 1) / GT, n_items);
-  k_gemm_f64<<<grid, 256, 0, st>>>(items, step);
+  launch_pdl(k_gemm_f64, grid, 256, 0, st, items, step);
 }
 
 // ---------------------------------------------------------------------------
@@ -133,6 +135,8 @@ __device__ __forceinline__ void split_bf16_d(double x, __nv_bfloat16& hi, __nv_b
 
 __global__ void __launch_bounds__(256) k_leap(const LeapItem* __restrict__ items, const int* step,
                                               double dt, int* counter, int* step_rw) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ double2 Xa[LT][LT + 1];
   __shared__ double2 Xb[LT][LT + 1];
   const LeapItem& it = items[blockIdx.y];
@@ -221,7 +225,7 @@ void launch_leap(const LeapItem* items, int n_items, int Np_max, int x_f32, cons
   const int nt = Np_max / LT;
   dim3 grid(nt * (nt + 1) / 2, n_items);
   dim3 block(LT, 8);
-  k_leap<<<grid, block, 0, st>>>(items, step, dt, counter, step_rw);
+  launch_pdl(k_leap, grid, block, 0, st, items, step, dt, counter, step_rw);
 }
 
 // ---------------------------------------------------------------------------
@@ -234,6 +238,8 @@ void launch_leap(const LeapItem* items, int n_items, int Np_max, int x_f32, cons
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_leap_split(const LeapItem* __restrict__ items, const int* step, double dt,
                                                     int* counter, int* step_rw) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ float2 Xa[LT][LT + 1];
   __shared__ float2 Xb[LT][LT + 1];
   const LeapItem& it = items[blockIdx.y];
@@ -312,7 +318,7 @@ void launch_leap_split(const LeapItem* items, int n_items, int Np_max, const int
   const int nt = Np_max / LT;
   dim3 grid(nt * (nt + 1) / 2, n_items);
   dim3 block(LT, 8);
-  k_leap_split<<<grid, block, 0, st>>>(items, step, dt, counter, step_rw);
+  launch_pdl(k_leap_split, grid, block, 0, st, items, step, dt, counter, step_rw);
 }
 
 // complex128 row-major Np x Np -> FP32 planar [Re(row) | Im(row)]

@@ -54,10 +54,12 @@ struct Variant {
   int bn, st, streamk, pair;
 };
 // tile width (per CTA, or per pair for the 2-SM variant), pipeline stages,
-// stream-K schedule, 2-SM pair (autotune candidates)
-constexpr Variant kVariants[] = {{256, 3, 0, 1}, {256, 3, 1, 1}, {256, 2, 0, 0}, {256, 2, 1, 0}, {128, 3, 0, 0},
-                                 {128, 3, 1, 0}};
-constexpr int kNumVariants = 6;
+// schedule (0 classic, 1 stream-K over all tiles, 2 whole waves classic and
+// stream-K over the rest), 2-SM pair.  Variant 0 is the default; all are
+// autotune candidates.
+constexpr Variant kVariants[] = {{256, 3, 0, 1}, {256, 3, 1, 1}, {256, 3, 2, 1}, {256, 2, 0, 0},
+                                 {256, 2, 1, 0}, {128, 3, 0, 0}, {128, 3, 1, 0}};
+constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
 template <int BN, int ST, int EPI>
 int smem_bytes() {
@@ -66,8 +68,7 @@ int smem_bytes() {
 
 template <int BN, int ST, int EPI>
 cudaError_t launch_t(const TcPlan* p, cudaStream_t st) {
-  k_tc_gemm<BN, ST, EPI><<<p->grid, 192, p->smem, st>>>(p->P);
-  return cudaGetLastError();
+  return launch_pdl(k_tc_gemm<BN, ST, EPI>, p->grid, 192, p->smem, st, p->P);
 }
 
 template <int ST, int EPI>
@@ -82,13 +83,15 @@ cudaError_t launch_pair(const TcPlan* p, cudaStream_t st) {
   cfg.blockDim = dim3(192, 1, 1);
   cfg.dynamicSmemBytes = p->smem;
   cfg.stream = st;
-  cudaLaunchAttribute attr[1];
+  cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = 2;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = 2;
   return cudaLaunchKernelEx(&cfg, k_tc_gemm2<ST, EPI>, p->P);
 }
 
@@ -212,6 +215,25 @@ static int build_one(const std::vector<TcSysView>& sys, const std::vector<DevIte
     plan->grid = pair ? (nsm & ~1) : nsm;  // pairs: workers are the nsm / 2 clusters
     plan->P.streamk = 1;
     plan->P.total_iters = iters;
+    // schedule 2: whole waves of tiles first (classic order), stream-K over the
+    // remainder; a remainder thinner than two k-iterations per worker is not
+    // shared that way.  Schedule 1: stream-K over every tile.
+    const int G = pair ? plan->grid / 2 : plan->grid;
+    int t0 = 0;
+    long long i0 = 0;
+    if (kVariants[variant].streamk == 2) {
+      t0 = (tiles / G) * G;
+      i0 = iters;
+      for (const TcProb& pr : probs)
+        if (t0 >= pr.tile0 && t0 < pr.tile0 + pr.tiles_m * pr.tiles_n)
+          i0 = pr.iter0 + (long long)(t0 - pr.tile0) * pr.kt;
+      if (iters - i0 < 2LL * G) {
+        t0 = 0;
+        i0 = 0;
+      }
+    }
+    plan->P.sk_tile0 = t0;
+    plan->P.sk_iter0 = i0;
     if (cudaMalloc(&plan->d_ws, sizeof(float) * (size_t)nsm * BM * BNv) != cudaSuccess ||
         cudaMalloc(&plan->d_flags, sizeof(int) * nsm) != cudaSuccess) {
       *msg = "cudaMalloc failed for the stream-K workspace";
@@ -224,24 +246,43 @@ static int build_one(const std::vector<TcSysView>& sys, const std::vector<DevIte
   return 0;
 }
 
+// median device time of 9 launches after 2 warm-up launches
 static double time_plan(TcPlan* p, cudaStream_t st) {
-  cudaEvent_t a, b;
-  cudaEventCreate(&a);
-  cudaEventCreate(&b);
+  constexpr int R = 9;
+  cudaEvent_t ev[R + 1];
+  for (auto& e : ev) cudaEventCreate(&e);
   launch_variant(p, st);
-  cudaEventRecord(a, st);
-  for (int i = 0; i < 3; ++i) launch_variant(p, st);
-  cudaEventRecord(b, st);
-  cudaEventSynchronize(b);
-  float ms = 0.f;
-  cudaEventElapsedTime(&ms, a, b);
-  cudaEventDestroy(a);
-  cudaEventDestroy(b);
-  return ms;
+  launch_variant(p, st);
+  cudaEventRecord(ev[0], st);
+  for (int i = 0; i < R; ++i) {
+    launch_variant(p, st);
+    cudaEventRecord(ev[i + 1], st);
+  }
+  cudaEventSynchronize(ev[R]);
+  float ms[R];
+  for (int i = 0; i < R; ++i) cudaEventElapsedTime(&ms[i], ev[i], ev[i + 1]);
+  for (auto& e : ev) cudaEventDestroy(e);
+  std::sort(ms, ms + R);
+  return ms[R / 2];
+}
+
+int tc_num_variants() { return kNumVariants; }
+
+int tc_variant_info(int v, int* out4) {
+  if (v < 0 || v >= kNumVariants) return -1;
+  out4[0] = kVariants[v].bn;
+  out4[1] = kVariants[v].st;
+  out4[2] = kVariants[v].streamk;
+  out4[3] = kVariants[v].pair;
+  return 0;
 }
 
 int tc_build_plans(const std::vector<TcSysView>& sys, const std::vector<DevItem>& items, long long timeout_ns,
-                   int autotune, cudaStream_t st, TcPlan** p1, TcPlan** p2, std::string* msg) {
+                   int autotune, int force_variant, cudaStream_t st, TcPlan** p1, TcPlan** p2, std::string* msg) {
+  if (force_variant >= kNumVariants) {
+    *msg = "tile variant index out of range";
+    return -1;
+  }
   *p1 = *p2 = nullptr;
   if (configure_all() != cudaSuccess) {
     *msg = "cannot raise the shared-memory limit of the tcgen05 kernels";
@@ -250,8 +291,9 @@ int tc_build_plans(const std::vector<TcSysView>& sys, const std::vector<DevItem>
   for (int epi = 0; epi < 2; ++epi) {
     TcPlan* best = nullptr;
     double best_ms = 1e30;
-    const int first = 0;  // the pair kernel handles every Np (a multiple of 128)
-    const int nv = autotune ? kNumVariants : first + 1;
+    // the pair kernel handles every Np (a multiple of 128), so variant 0 always applies
+    const int first = force_variant >= 0 ? force_variant : 0;
+    const int nv = force_variant >= 0 ? first + 1 : (autotune ? kNumVariants : first + 1);
     for (int v = first; v < nv; ++v) {
       TcPlan* p = new TcPlan();
       if (build_one(sys, items, epi, v, timeout_ns, p, msg)) {

@@ -47,11 +47,16 @@ struct TcParams {
   int n_prob, total_tiles, nseg;
   int* err;
   long long timeout_ns;
-  // stream-K schedule (streamk != 0): CTA c owns the global k-iterations
-  // [total_iters c / G, total_iters (c+1) / G); a tile shared by several CTAs
-  // is finished by the CTA holding its k = 0 part, after adding the FP32
-  // partials that the others left in ws[cta] and announced in flags[cta].
+  // stream-K schedule (streamk != 0): the tiles below sk_tile0 (whole waves)
+  // go to the workers in turn, as in the classic schedule, so that workers on
+  // the same operand rows stay at the same k and share them through L2; worker c
+  // then owns the global k-iterations [i0 + R c / G, i0 + R (c+1) / G) of the
+  // rest, i0 = sk_iter0, R = total_iters - i0.  A tile shared by several
+  // workers is finished by the one holding its k = 0 part, after adding the
+  // FP32 partials that the others left in ws[worker] and announced in flags.
   int streamk;
+  int sk_tile0;
+  long long sk_iter0;
   long long total_iters;
   float* ws;           // [G][BM][BN]
   int* flags;          // [G], 1 = partial ready (reset to 0 by the finishing CTA)
@@ -189,7 +194,7 @@ struct UnitCursor {
 
 // first global k-iteration of worker c out of G (a worker is a CTA, or a CTA pair)
 __device__ __forceinline__ long long sk_start(const TcParams& P, int c, int G) {
-  return P.total_iters * (long long)c / (long long)G;
+  return P.sk_iter0 + (P.total_iters - P.sk_iter0) * (long long)c / (long long)G;
 }
 
 __device__ __forceinline__ void cursor_init(const TcParams& P, UnitCursor& u, int c, int G) {
@@ -202,6 +207,16 @@ __device__ __forceinline__ void cursor_init(const TcParams& P, UnitCursor& u, in
 // next unit: global tile t, its k-iterations [kb, ke) out of KT; false when done
 __device__ __forceinline__ bool cursor_next(const TcParams& P, UnitCursor& u, int G, int& t, int& kb, int& ke,
                                             int& KT) {
+  const int t_classic = P.streamk ? P.sk_tile0 : P.total_tiles;
+  if (u.t_next < t_classic) {
+    t = u.t_next;
+    u.t_next += G;
+    u.p = find_prob(P.probs, P.n_prob, t, u.p);
+    KT = P.nseg * (2 * P.probs[u.p].Np) / BK;
+    kb = 0;
+    ke = KT;
+    return true;
+  }
   if (P.streamk) {
     if (u.it >= u.e) return false;
     while (u.p + 1 < P.n_prob && P.probs[u.p + 1].iter0 <= u.it) ++u.p;
@@ -216,14 +231,7 @@ __device__ __forceinline__ bool cursor_next(const TcParams& P, UnitCursor& u, in
     u.it = tile_start + ke;
     return true;
   }
-  if (u.t_next >= P.total_tiles) return false;
-  t = u.t_next;
-  u.t_next += G;
-  u.p = find_prob(P.probs, P.n_prob, t, u.p);
-  KT = P.nseg * (2 * P.probs[u.p].Np) / BK;
-  kb = 0;
-  ke = KT;
-  return true;
+  return false;
 }
 
 // last worker that holds part of the tile whose k = 0 part ends worker c's range
@@ -298,6 +306,10 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcPa
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   volatile int* s_epi_ok = abort_flag + 1;  // indexed by unit parity
+  // barriers and TMEM are set up; operands and outputs are touched only after
+  // the preceding kernel of the step has completed
+  pdl_wait();
+  pdl_trigger();
 
   if (warp == 0) {
     if (lane == 0) {
@@ -601,6 +613,8 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm2(const __grid_constant__ TcP
   cluster_sync_all();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
+  pdl_wait();
+  pdl_trigger();
   const uint32_t full_l = map_to_rank0(full0), acce_l = map_to_rank0(acce0);
   const int pair = blockIdx.x >> 1, G2 = gridDim.x >> 1;
 

@@ -1206,8 +1206,8 @@ int vgtb_create_batch(vgtb_ctx** out, int n_sys, const vgtb_system* sys, int n_t
       views[s].Wemb_p = fam[s].Wemb;
     }
     std::string msg;
-    if (tc_build_plans(views, ctx->items_h, ctx->opt.timeout_ns, ctx->opt.autotune, ctx->stream, &ctx->tc1, &ctx->tc2,
-                       &msg))
+    if (tc_build_plans(views, ctx->items_h, ctx->opt.timeout_ns, ctx->opt.autotune, -1, ctx->stream, &ctx->tc1,
+                       &ctx->tc2, &msg))
       return bail(fail(ctx, VGTB_E_CUDA, "tcgen05 plan: %s", msg.c_str()));
   }
   if (ctx->opt.init == VGTB_INIT_GROUND) {
@@ -1578,6 +1578,12 @@ int vgtb_kernel_stats(vgtb_ctx* ctx, long long* launches, double* ms, int n) {
     if (ms) ms[c] = ctx->prof_ms[c];
   }
   return VGTB_K_COUNT;
+}
+
+int vgtb_tile_config(const vgtb_ctx* ctx, int product, int* cfg) {
+  if (!ctx || !cfg || (product != 1 && product != 2)) return VGTB_E_INVALID;
+  if (!ctx->split) return VGTB_E_STATE;
+  return tc_variant_info(tc_plan_variant(product == 1 ? ctx->tc1 : ctx->tc2), cfg) == 0 ? VGTB_OK : VGTB_E_STATE;
 }
 
 const char* vgtb_last_error(const vgtb_ctx* ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }

@@ -36,6 +36,14 @@ void to_padded(const double* src, std::vector<double2>& dst, int n, int Np) {
 
 extern "C" int vgtb_diag_split_chain(int n, const double* a, const double* r, const double* s, double* w_out,
                                      double* x_out) {
+  return vgtb_diag_split_chain_variant(n, a, r, s, -1, w_out, x_out);
+}
+
+extern "C" int vgtb_diag_num_variants() { return tc_num_variants(); }
+
+extern "C" int vgtb_diag_split_chain_variant(int n, const double* a, const double* r, const double* s, int variant,
+                                             double* w_out, double* x_out) {
+  if (variant >= tc_num_variants()) return VGTB_E_INVALID;
   if (n < 1 || !a || !r || !s || !w_out || !x_out) return VGTB_E_INVALID;
   if (!tc_gemm_supported()) return VGTB_E_UNSUPPORTED;
   const int Np = (n + 127) / 128 * 128;
@@ -80,7 +88,7 @@ extern "C" int vgtb_diag_split_chain(int n, const double* a, const double* r, co
   items[0].Xf = xf;
   TcPlan *p1 = nullptr, *p2 = nullptr;
   std::string msg;
-  if (tc_build_plans(views, items, 2000000000LL, 0, st, &p1, &p2, &msg)) return VGTB_E_CUDA;
+  if (tc_build_plans(views, items, 2000000000LL, 0, variant, st, &p1, &p2, &msg)) return VGTB_E_CUDA;
   int rc = VGTB_OK;
   if (tc_launch(p1, st) || tc_launch(p2, st)) rc = VGTB_E_CUDA;
   if (cudaDeviceSynchronize() != cudaSuccess) rc = VGTB_E_CUDA;

@@ -18,6 +18,31 @@
 
 namespace vgtb {
 
+// Programmatic dependent launch: the step kernels are launched with
+// programmatic stream serialization, so a kernel's CTAs may be scheduled while
+// its predecessor drains.  Every CTA calls pdl_wait() before its first access
+// to memory that an earlier kernel writes (and before any early return, so
+// that a grid never completes ahead of its predecessor); pdl_wait() returns
+// once the preceding grid has completed and its writes are visible.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 constexpr double kLight = 137.035999084;
 
 // status bits written by kernels

@@ -24,9 +24,14 @@ struct TcSysView {
 // Plans for the two products of the split form, over every item:
 //   product 1: W = [dD | D0] [H | dH]^dagger  -> embedded BF16 hi/lo pieces of W
 //   product 2: X = S^-1 W^dagger               -> FP32 planar X
+// force_variant >= 0 uses that tile variant for both; otherwise variant 0, or
+// with autotune the fastest candidate (median of 9 timed launches) per product.
 // Returns 0 on success, else fills *msg.
 int tc_build_plans(const std::vector<TcSysView>& sys, const std::vector<DevItem>& items, long long timeout_ns,
-                   int autotune, cudaStream_t st, TcPlan** p1, TcPlan** p2, std::string* msg);
+                   int autotune, int force_variant, cudaStream_t st, TcPlan** p1, TcPlan** p2, std::string* msg);
+int tc_num_variants();
+// {tile width, pipeline stages, schedule (0 classic, 1 stream-K, 2 classic waves + stream-K rest), 2-SM pair}
+int tc_variant_info(int v, int* out4);
 int tc_launch(TcPlan* p, cudaStream_t st);
 int tc_status(TcPlan* p, cudaStream_t st);  // 0 or the plan's device error word
 void tc_destroy_plan(TcPlan* p);

@@ -32,7 +32,8 @@ EXPORTS = ["vgtb_default_options", "vgtb_create", "vgtb_create_batch", "vgtb_set
            "vgtb_get_density", "vgtb_get_initial_density", "vgtb_state_size", "vgtb_get_state", "vgtb_set_state",
            "vgtb_profile", "vgtb_kernel_stats", "vgtb_last_error", "vgtb_destroy",
            "vgtb_diag_split_chain", "vgtb_split_cgemm_noalloc", "vgtb_spectrum", "vgtb_group_charges",
-           "vgtb_set_coefficients", "vgtb_get_coefficients"]
+           "vgtb_set_coefficients", "vgtb_get_coefficients", "vgtb_tile_config",
+           "vgtb_diag_split_chain_variant", "vgtb_diag_num_variants"]
 
 
 class VgtbSystem(C.Structure):
@@ -94,6 +95,9 @@ def load(path: str = LIB_PATH):
     lib.vgtb_group_charges.argtypes = [ctxp, I, I, P(I), P(D)]
     lib.vgtb_set_coefficients.argtypes = [ctxp, I, I, I, P(D)]
     lib.vgtb_get_coefficients.argtypes = [ctxp, I, I, P(D)]
+    lib.vgtb_tile_config.argtypes = [ctxp, I, P(I)]
+    lib.vgtb_diag_split_chain_variant.argtypes = [I, P(D), P(D), P(D), I, P(D), P(D)]
+    lib.vgtb_diag_num_variants.argtypes = []
     for name in EXPORTS:
         if name not in ("vgtb_default_options", "vgtb_last_error", "vgtb_destroy", "vgtb_state_size"):
             getattr(lib, name).restype = I
@@ -160,19 +164,24 @@ def default_options(**kw) -> VgtbOptions:
     return o
 
 
-def diag_split_chain(a, r, s):
+def diag_split_chain(a, r, s, variant: int = -1):
     """Run the two tcgen05 split-precision products on host matrices:
-    W = a r^dagger and X = s W^dagger.  Returns (W, X) as complex128 arrays."""
+    W = a r^dagger and X = s W^dagger, with tile variant `variant` (-1 = default).
+    Returns (W, X) as complex128 arrays."""
     lib = load()
     a, r, s = (np.ascontiguousarray(x, np.complex128) for x in (a, r, s))
     n = a.shape[0]
     w = np.zeros((n, n), np.complex128)
     x = np.zeros((n, n), np.complex128)
     cp = lambda m: m.ctypes.data_as(C.POINTER(C.c_double))  # noqa: E731
-    rc = lib.vgtb_diag_split_chain(n, cp(a), cp(r), cp(s), cp(w), cp(x))
+    rc = lib.vgtb_diag_split_chain_variant(n, cp(a), cp(r), cp(s), int(variant), cp(w), cp(x))
     if rc != VGTB_OK:
-        raise VgtbError(rc, "vgtb_diag_split_chain failed")
+        raise VgtbError(rc, "vgtb_diag_split_chain_variant failed")
     return w, x
+
+
+def num_tile_variants() -> int:
+    return load().vgtb_diag_num_variants()
 
 
 class Context:
@@ -291,6 +300,13 @@ class Context:
 
     def profile(self, enable: bool = True):
         self._check(load().vgtb_profile(self._h, 1 if enable else 0))
+
+    def tile_config(self, product: int):
+        """{"tile_n", "stages", "schedule", "pair"} of tcgen05 product 1 or 2 (split contexts)."""
+        cfg = (C.c_int * 4)()
+        self._check(load().vgtb_tile_config(self._h, int(product), cfg))
+        return {"tile_n": cfg[0], "stages": cfg[1],
+                "schedule": ("classic", "stream-K", "classic waves + stream-K")[cfg[2]], "pair": bool(cfg[3])}
 
     def kernel_stats(self):
         n = len(KERNEL_CLASSES)

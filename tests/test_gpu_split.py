@@ -38,6 +38,24 @@ def test_split_products_match_numpy(n):
     assert rel_fro([x], [s @ w_ref]) > 0.1
 
 
+@pytest.mark.parametrize("n", [384, 1000, 2048])
+def test_every_tile_variant_matches_numpy(n):
+    """Each schedule the autotuner may pick, forced on its own.  At n = 2048 the
+    128 pair tiles fill one whole wave of 76 pairs and leave 52 tiles to the
+    stream-K part of the mixed schedule."""
+    from paper_2308_09782_gb300 import vgtb
+    rng = np.random.default_rng(7 + n)
+    def rnd():
+        return rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n))
+    a, r, s = rnd(), rnd(), rnd()
+    w_ref = a @ r.conj().T
+    x_ref = s @ w_ref.conj().T
+    for v in range(vgtb.num_tile_variants()):
+        w, x = vgtb.diag_split_chain(a, r, s, variant=v)
+        assert rel_fro([w], [w_ref]) < 3e-5, v
+        assert rel_fro([x], [x_ref]) < 6e-5, v
+
+
 @pytest.mark.parametrize("name,nsteps", [("si8_pulse", 1000), ("si64_pulse", 2000)])
 def test_split_propagation_matches_oracle(name, nsteps):
     from paper_2308_09782_gb300 import vgtb
