@@ -46,6 +46,8 @@ def parse():
     p.add_argument("--impl", choices=["native", "reference"], default="native")
     p.add_argument("--fp64-steps", type=int, default=20)
     p.add_argument("--cpu-steps", type=int, default=6)
+    p.add_argument("--tiles", default="auto",
+                   help="tcgen05 tile variants of product 1,2 (e.g. 1,0) instead of the autotuner's choice")
     p.add_argument("--cn-steps", type=int, default=4,
                    help="timed steps of the FP64 Crank-Nicolson integrator (0 = skip)")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -181,18 +183,20 @@ def measured_peaks():
         return {}
 
 
-def kernel_traffic(kernel: str, per_launch_units: float):
+def kernel_traffic(kernel: str, per_launch_units: float, tile=None):
     """DRAM bytes per launch from the committed ncu summary, if the kernel source
-    is unchanged since the capture; None otherwise."""
+    is unchanged since the capture and (for the products) the capture ran the
+    same tile variant; None otherwise."""
     try:
-        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[kernel]
+        recs = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[kernel]
     except (OSError, KeyError, ValueError):
         return None
-    src = os.path.join(ROOT, rec["source"])
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    if h != rec["sha256"]:
-        return None
-    return rec["bytes_per_unit"] * per_launch_units
+    for rec in (recs if isinstance(recs, list) else [recs]):
+        src = os.path.join(ROOT, rec["source"])
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        if h == rec["sha256"] and (tile is None or rec.get("tile") == tile):
+            return rec["bytes_per_unit"] * per_launch_units
+    return None
 
 
 # ---------------------------------------------------------------------------
@@ -258,11 +262,15 @@ def native(args):
     if A.shape[0] < n_need:                      # the kick is constant after t = 0
         A = np.tile(A[:1], (n_need, 1))
     stream = torch.cuda.current_stream()
+    tile_opts = {"autotune": 1}
+    if args.tiles != "auto":
+        tile_opts = {"autotune": 0, "tile_variant": [int(x) for x in args.tiles.split(",")]}
     ctx = vgtb.Context(sysd, precision=vgtb.SPLIT_BF16X3, init=vgtb.INIT_GROUND,
-                       cuda_stream=stream.cuda_stream, graph_steps=50, autotune=1)
+                       cuda_stream=stream.cuda_stream, graph_steps=50, **tile_opts)
     ctx.set_field(0, A[:n_need])
     tiles = {f"product{p}": ctx.tile_config(p) for p in (1, 2)}
-    tiles["choice"] = "autotuned at create: fastest of the tcgen05 tile variants (median of 9 launches)"
+    tiles["choice"] = ("autotuned at create: fastest of the tcgen05 tile variants (median of 9 launches)"
+                       if args.tiles == "auto" else f"forced: variants {args.tiles}")
     ctx.profile(True)
     ctx.propagate(W)
     ctx.profile(True)                            # reset the per-kernel counters
@@ -273,7 +281,9 @@ def native(args):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
+    torch.cuda.nvtx.range_push("split_timed")
     ctx.propagate(K)
+    torch.cuda.nvtx.range_pop()
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -295,7 +305,9 @@ def native(args):
     f0 = torch.cuda.Event(enable_timing=True)
     f1 = torch.cuda.Event(enable_timing=True)
     f0.record(stream)
+    torch.cuda.nvtx.range_push("fp64_timed")
     cf.propagate(Kf)
+    torch.cuda.nvtx.range_pop()
     f1.record(stream)
     torch.cuda.synchronize()
     ms_f = max_over_ranks(f0.elapsed_time(f1))
@@ -317,7 +329,9 @@ def native(args):
         c0 = torch.cuda.Event(enable_timing=True)
         c1 = torch.cuda.Event(enable_timing=True)
         c0.record(stream)
+        torch.cuda.nvtx.range_push("cn_timed")
         cc.propagate(Kc)
+        torch.cuda.nvtx.range_pop()
         c1.record(stream)
         torch.cuda.synchronize()
         ms_c = max_over_ranks(c0.elapsed_time(c1))
@@ -408,7 +422,8 @@ def native(args):
         "roofline": {"bound": "tensor", "kernel": "k_tc_gemm (product 1: W = [dD|D0][H|dH]^dagger)",
                      "achieved": round(ach1, 1), "peak": peak, "unit": "TFLOP/s",
                      "frac": round(ach1 / peak, 4), "peak_kind": peak_kind,
-                     "traffic": kernel_traffic("tc_gemm1", 1.0),
+                     "frac_of_burst": round(ach1 / peaks.get("bf16_tflops", 1900.0), 4),
+                     "traffic": kernel_traffic("tc_gemm1", 1.0, tiles["product1"]),
                      "flops_per_launch": flops1, "avg_launch_ms": round(avg1, 4),
                      "product2_achieved": round(ach2, 1), "product2_frac": round(ach2 / peak, 4)},
         "kernel_ms_per_step": {k: round(v, 4) for k, v in kern_ms.items()},
@@ -445,9 +460,14 @@ def batched(args):
                 fields.append(inputs.pulse_field(nsteps, 0.2, 0.01, w, pol=pol))
     stream = torch.cuda.current_stream()
     t0 = time.perf_counter()
+    tile_opts = {"autotune": 1}
+    if args.tiles != "auto":
+        tile_opts = {"autotune": 0, "tile_variant": [int(x) for x in args.tiles.split(",")]}
     ctx = vgtb.Context(systems, traj_sys=traj_sys, precision=vgtb.SPLIT_BF16X3, init=vgtb.INIT_GROUND,
-                       cuda_stream=stream.cuda_stream, graph_steps=20, obs_stride=10, autotune=1)
+                       cuda_stream=stream.cuda_stream, graph_steps=20, obs_stride=10, **tile_opts)
     t_setup = time.perf_counter() - t0
+    tiles = {f"product{p}": ctx.tile_config(p) for p in (1, 2)}
+    tiles["choice"] = "autotuned at create" if args.tiles == "auto" else f"forced: variants {args.tiles}"
     for t, f in enumerate(fields):
         ctx.set_field(t, f)
     ctx.profile(True)
@@ -460,7 +480,9 @@ def batched(args):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
+    torch.cuda.nvtx.range_push("split_timed")
     ctx.propagate(K)
+    torch.cuda.nvtx.range_pop()
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -475,6 +497,7 @@ def batched(args):
     g1 = stats["gemm1"][1] / max(stats["gemm1"][0], 1)
     g2 = stats["gemm2"][1] / max(stats["gemm2"][0], 1)
     peak = measured_peaks().get("bf16_tflops_sustained", 1700.0)
+    burst = measured_peaks().get("bf16_tflops", 1900.0)
     steps_s = world * K / (ms / 1e3)
     if rank != 0:
         return
@@ -482,10 +505,13 @@ def batched(args):
             "unit": "steps/s", "n_gpus": world, "steps": K, "warmup": W, "ms_per_step": round(ms / K, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "bf16x3 (f32 accumulate) + f64 master", "data": "synthetic",
-            "config": {"workload": BATCH_WORKLOAD, "setup_s": round(t_setup, 1)},
+            "config": {"workload": BATCH_WORKLOAD, "setup_s": round(t_setup, 1), "tiles": tiles},
             "trajectory_steps_per_s": round(18 * steps_s, 1), "k_propagation_steps_per_s": round(144 * steps_s, 1),
             "roofline": {"bound": "tensor", "achieved": round(flops1 / (g1 * 1e-3) / 1e12, 1), "peak": peak,
                          "unit": "TFLOP/s", "frac": round(flops1 / (g1 * 1e-3) / 1e12 / peak, 4),
+                         "peak_kind": "measured sustained bf16 (MEASURED_PEAKS.json; its clocks under load "
+                                      "had a 1470 MHz median, this run's are in clocks)",
+                         "frac_of_burst": round(flops1 / (g1 * 1e-3) / 1e12 / burst, 4),
                          "product2_frac": round(flops2 / (g2 * 1e-3) / 1e12 / peak, 4)},
             "kernel_ms_per_step": {k: round(v[1] / max(v[0], 1), 4) for k, v in stats.items()},
             "gpu_launches": 7 * K + 3, "clocks": clocks}

@@ -112,9 +112,11 @@ typedef struct {
                                sweeps contract by dt/2 max|eig(S^-1 H)| each */
   double cn_tol;            /* Crank-Nicolson: propagate() fails with E_UNSTABLE when the last
                                two iterates differ by more than cn_tol in any entry (0 = 1e-10) */
+  int tile_variant[2];      /* split form: tile variant of product 1 / product 2 (see
+                               vgtb_tile_config; -1 = variant 0, or the autotuner's choice) */
 } vgtb_options;
 
-/* Fill *opt with the defaults above (precision FP64, ground-state init). */
+/* Fill *opt with the defaults above (precision FP64, ground-state init, leapfrog). */
 void vgtb_default_options(vgtb_options* opt);
 
 /* Create a context for one system and one trajectory (Sec. 2 problem statement).

@@ -212,10 +212,22 @@ __global__ void k_obs0(const DevSys* __restrict__ sysv, int s_idx) {
     for (int i = 0; i < 5; ++i) S.obs0[5LL * tg + i] = v[i];
 }
 
-void launch_obs0(const DevSys* sys, int s_idx, int n_tgt, cudaStream_t st) {
+// Setup (split form): obs0a[I] = obs0 summed over the targets of row atom I, in target order.
+__global__ void k_obs0_atoms(const DevSys* __restrict__ sysv, int s_idx) {
+  const DevSys& S = sysv[s_idx];
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= S.nat) return;
+  double v[5] = {0, 0, 0, 0, 0};
+  for (int tg = S.atom_tgt0[I]; tg < S.atom_tgt0[I + 1]; ++tg)
+    for (int i = 0; i < 5; ++i) v[i] += S.obs0[5LL * tg + i];
+  for (int i = 0; i < 5; ++i) S.obs0a[5LL * I + i] = v[i];
+}
+
+void launch_obs0(const DevSys* sys, int s_idx, int n_tgt, int nat, int split, cudaStream_t st) {
   const int threads = 256;
   const int blocks = (n_tgt * 16 + threads - 1) / threads;
   k_obs0<<<blocks, threads, 0, st>>>(sys, s_idx);
+  if (split) k_obs0_atoms<<<(nat + 127) / 128, 128, 0, st>>>(sys, s_idx);
 }
 
 __device__ __forceinline__ float half_sum_f(float v) {
@@ -226,9 +238,12 @@ __device__ __forceinline__ float half_sum_f(float v) {
 
 // ---------------------------------------------------------------------------
 // k_obs of the split form: the dD sums in FP32 (dD converted from the FP64
-// master with integer operations, k-space blocks as packed FP32 records), the
-// constant D0 part (obs0) and the A terms in FP64.  The FP32 rounding of the
-// dD part is far below the BF16x3 products' own error.
+// master with integer operations, k-space blocks as packed FP32 records),
+// written per target as FP32.  GB300 issues an FP64 warp instruction at a small
+// fraction of the FP32 rate, whatever the number of active lanes, so the FP64
+// work (the constant D0 part, the A terms, the sums over targets) moves to the
+// per-atom warps of k_scc_atoms.  The FP32 rounding of the dD part is far below
+// the BF16x3 products' own error.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_obs_split(const DevSys* __restrict__ sysv, const DevTraj* __restrict__ trj,
                                                    const DevItem* __restrict__ items, const int* __restrict__ wpre,
@@ -278,24 +293,14 @@ __global__ void __launch_bounds__(256) k_obs_split(const DevSys* __restrict__ sy
   sz = half_sum_f(sz);
   sH = half_sum_f(sH);
   if (U.active && lane == 0) {
-    const double* o = S.obs0 + 5LL * U.tg;
-    const double dS = o[0] + f2d_bits(sS), dx = o[1] + f2d_bits(sx), dy = o[2] + f2d_bits(sy);
-    const double dz = o[3] + f2d_bits(sz), dH = o[4] + f2d_bits(sH);
-    double A0 = 0.0, A1 = 0.0, A2 = 0.0;
-    if (T.A) {
-      A0 = T.A[3 * n];
-      A1 = T.A[3 * n + 1];
-      A2 = T.A[3 * n + 2];
-    }
-    constexpr double ic = 1.0 / kLight;
-    const double a0 = A0 * ic, a1 = A1 * ic, a2 = A2 * ic;
-    const double alpha = 0.5 * (a0 * a0 + a1 * a1 + a2 * a2);
-    double* p = T.part + 5LL * U.tg;
-    p[0] = dS;
-    p[1] = dx + a0 * dS;
-    p[2] = dy + a1 * dS;
-    p[3] = dz + a2 * dS;
-    p[4] = dH + (a0 * dx + a1 * dy + a2 * dz) + alpha * dS;
+    // the D0 part and the A terms are added per atom in k_scc_atoms (both are
+    // linear in the target sums), so this kernel issues no FP64 instruction
+    float* p = T.partf + 5LL * U.tg;
+    p[0] = sS;
+    p[1] = sx;
+    p[2] = sy;
+    p[3] = sz;
+    p[4] = sH;
   }
 }
 
@@ -353,13 +358,41 @@ __global__ void __launch_bounds__(kSccThreads) k_scc_atoms(const DevSys* __restr
   if (I >= S.nat) return;
   const int n = fixed_step >= 0 ? fixed_step : *step;
   double v[5] = {0, 0, 0, 0, 0};
-  for (int tg = S.atom_tgt0[I] + lane; tg < S.atom_tgt0[I + 1]; tg += 32) {
-    const double* p = T.part + 5LL * tg;
+  if (T.partf) {
+    // split form: FP32 target sums of dD, then D0 part and A terms once per atom
+    for (int tg = S.atom_tgt0[I] + lane; tg < S.atom_tgt0[I + 1]; tg += 32) {
+      const float* p = T.partf + 5LL * tg;
 #pragma unroll
-    for (int i = 0; i < 5; ++i) v[i] += p[i];
+      for (int i = 0; i < 5; ++i) v[i] += f2d_bits(p[i]);
+    }
+#pragma unroll
+    for (int i = 0; i < 5; ++i) v[i] = warp_sum(v[i]);
+    const double* o = S.obs0a + 5LL * I;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) v[i] += o[i];
+    double A0 = 0.0, A1 = 0.0, A2 = 0.0;
+    if (T.A) {
+      A0 = T.A[3 * n];
+      A1 = T.A[3 * n + 1];
+      A2 = T.A[3 * n + 2];
+    }
+    constexpr double ic = 1.0 / kLight;
+    const double a0 = A0 * ic, a1 = A1 * ic, a2 = A2 * ic;
+    const double alpha = 0.5 * (a0 * a0 + a1 * a1 + a2 * a2);
+    const double dS = v[0], dx = v[1], dy = v[2], dz = v[3], dH = v[4];
+    v[1] = dx + a0 * dS;
+    v[2] = dy + a1 * dS;
+    v[3] = dz + a2 * dS;
+    v[4] = dH + (a0 * dx + a1 * dy + a2 * dz) + alpha * dS;
+  } else {
+    for (int tg = S.atom_tgt0[I] + lane; tg < S.atom_tgt0[I + 1]; tg += 32) {
+      const double* p = T.part + 5LL * tg;
+#pragma unroll
+      for (int i = 0; i < 5; ++i) v[i] += p[i];
+    }
+#pragma unroll
+    for (int i = 0; i < 5; ++i) v[i] = warp_sum(v[i]);
   }
-#pragma unroll
-  for (int i = 0; i < 5; ++i) v[i] = warp_sum(v[i]);
   if (lane == 0) {
     T.dq[I] = v[0] - S.z[I];
     if (record && T.q && n % stride == 0) T.q[(long long)(n / stride) * S.nat + I] = v[0];
@@ -406,6 +439,10 @@ __global__ void __launch_bounds__(kSccThreads) k_scc_eps(const DevSys* __restric
       T.eps[I] = e;
       T.erow[I] = dq[I] * e;
       if (T.eps_lv) T.eps_lv[(long long)(n & 1) * S.nat + I] = e;
+      if (T.epsf) {
+        T.epsf[I] = (float)e;
+        T.depsf[I] = (float)(e - S.eps0[I]);
+      }
       __threadfence();
     }
   }
@@ -448,6 +485,10 @@ __global__ void __launch_bounds__(kSccThreads) k_scc_eps(const DevSys* __restric
       T.J[3LL * n + 1] = J1;
       T.J[3LL * n + 2] = J2;
       T.E[n] = E;
+    }
+    if (T.af) {
+      constexpr double inv_c = 1.0 / kLight;
+      for (int a = 0; a < 3; ++a) T.af[a] = T.A ? (float)(T.A[3 * n + a] * inv_c) : 0.f;
     }
     int st = 0;
     if (!isfinite(J0) || !isfinite(J1) || !isfinite(J2) || !isfinite(E) || !isfinite(w[5])) st |= ST_NONFINITE;
@@ -589,21 +630,16 @@ __global__ void __launch_bounds__(256) k_phase_split(const DevSys* __restrict__ 
   const int lane = threadIdx.x & 15;
   const DevTraj& T = trj[U.t];
   const DevSys& S = sysv[T.sys];
-  const int n = *step;
-  float a0 = 0.f, a1 = 0.f, a2 = 0.f;
-  if (T.A) {  // multiply by the compile-time reciprocal: an FP64 division is a long sequence on GB300
-    constexpr double inv_c = 1.0 / kLight;
-    a0 = (float)(T.A[3 * n] * inv_c);
-    a1 = (float)(T.A[3 * n + 1] * inv_c);
-    a2 = (float)(T.A[3 * n + 2] * inv_c);
-  }
+  // A(t_n)/c and the shifts as FP32, prepared once per step by k_scc_eps: the
+  // kernel issues no FP64 instruction (each costs a warp many FP32 issue slots)
+  const float a0 = T.af[0], a1 = T.af[1], a2 = T.af[2];
   const int I = S.tgt_I[U.tg], J = S.tgt_J[U.tg];
   const int oi = S.orb_off[I], ni = S.orb_off[I + 1] - oi;
   const int oj = S.orb_off[J], nj = S.orb_off[J + 1] - oj;
   const int nel = ni * nj;
   const int g0 = S.tgt_img0[U.tg], g1 = S.tgt_img0[U.tg + 1];
-  const float beta = (float)(0.5 * (T.eps[I] + T.eps[J]));
-  const float dbeta = (float)(0.5 * ((T.eps[I] - S.eps0[I]) + (T.eps[J] - S.eps0[J])));
+  const float beta = 0.5f * (T.epsf[I] + T.epsf[J]);
+  const float dbeta = 0.5f * (T.depsf[I] + T.depsf[J]);
   for (int k = 0; k < S.nk; ++k) {
     const DevItem& it = items[T.item0 + k];
     for (int e = lane; e < nel; e += 16) {

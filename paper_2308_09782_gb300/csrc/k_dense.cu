@@ -273,21 +273,32 @@ __global__ void __launch_bounds__(256) k_leap_split(const LeapItem* __restrict__
     const double coef = euler ? dt : 2.0 * dt;
     const double2* base = euler ? it.D[cur] : it.D[nxt];
     const long long P = 2LL * Np * Np;
+    constexpr int RPT = LT / 8;  // rows per thread
     for (int half = 0; half < (bi == bj ? 1 : 2); ++half) {
       const int gi0 = half == 0 ? bi : bj, gj0 = half == 0 ? bj : bi;
-      for (int r = ty; r < LT; r += 8) {
+      // all loads of the thread's rows first (D_{n-1} is overwritten in place,
+      // element by element, by the same thread), then the updates and stores
+      float r0r[RPT], r0i[RPT];
+      double2 b[RPT];
+#pragma unroll
+      for (int j = 0; j < RPT; ++j) {
+        const int r = ty + 8 * j;
+        const long long idx = (long long)(gi0 * LT + r) * Np + gj0 * LT + tx;
+        const long long pr = (long long)(gi0 * LT + r) * 2 * Np + gj0 * LT + tx;
+        r0r[j] = it.R0f ? it.R0f[pr] : 0.f;
+        r0i[j] = it.R0f ? it.R0f[pr + Np] : 0.f;
+        b[j] = base[idx];
+      }
+#pragma unroll
+      for (int j = 0; j < RPT; ++j) {
+        const int r = ty + 8 * j;
         const float2 xij = half == 0 ? Xa[r][tx] : Xb[r][tx];
         const float2 xji = half == 0 ? Xb[tx][r] : Xa[tx][r];
         const long long idx = (long long)(gi0 * LT + r) * Np + gj0 * LT + tx;
         const long long pr = (long long)(gi0 * LT + r) * 2 * Np + gj0 * LT + tx;
-        float dr = xij.y + xji.y;
-        float di = -(xij.x - xji.x);
-        if (it.R0f) {
-          dr = it.R0f[pr] + dr;
-          di = it.R0f[pr + Np] + di;
-        }
-        const double2 b = base[idx];
-        const double2 v = make_double2(fma(coef, f2d_bits(dr), b.x), fma(coef, f2d_bits(di), b.y));
+        const float dr = r0r[j] + (xij.y + xji.y);
+        const float di = r0i[j] + (-(xij.x - xji.x));
+        const double2 v = make_double2(fma(coef, f2d_bits(dr), b[j].x), fma(coef, f2d_bits(di), b[j].y));
         it.D[nxt][idx] = v;
         const float fr = d2f_bits(v.x), fi = d2f_bits(v.y);
         const __nv_bfloat16 rh = __float2bfloat16_rn(fr), ih = __float2bfloat16_rn(fi);

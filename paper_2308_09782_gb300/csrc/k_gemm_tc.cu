@@ -278,8 +278,9 @@ int tc_variant_info(int v, int* out4) {
 }
 
 int tc_build_plans(const std::vector<TcSysView>& sys, const std::vector<DevItem>& items, long long timeout_ns,
-                   int autotune, int force_variant, cudaStream_t st, TcPlan** p1, TcPlan** p2, std::string* msg) {
-  if (force_variant >= kNumVariants) {
+                   int autotune, const int force_variant[2], cudaStream_t st, TcPlan** p1, TcPlan** p2,
+                   std::string* msg) {
+  if (force_variant[0] >= kNumVariants || force_variant[1] >= kNumVariants) {
     *msg = "tile variant index out of range";
     return -1;
   }
@@ -292,8 +293,9 @@ int tc_build_plans(const std::vector<TcSysView>& sys, const std::vector<DevItem>
     TcPlan* best = nullptr;
     double best_ms = 1e30;
     // the pair kernel handles every Np (a multiple of 128), so variant 0 always applies
-    const int first = force_variant >= 0 ? force_variant : 0;
-    const int nv = force_variant >= 0 ? first + 1 : (autotune ? kNumVariants : first + 1);
+    const int fv = force_variant[epi];
+    const int first = fv >= 0 ? fv : 0;
+    const int nv = fv >= 0 ? first + 1 : (autotune ? kNumVariants : first + 1);
     for (int v = first; v < nv; ++v) {
       TcPlan* p = new TcPlan();
       if (build_one(sys, items, epi, v, timeout_ns, p, msg)) {

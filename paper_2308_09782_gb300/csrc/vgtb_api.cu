@@ -67,6 +67,10 @@ struct HostTraj {
   double* dq = nullptr;
   double* eps = nullptr;
   double* eps_lv = nullptr;
+  float* epsf = nullptr;
+  float* depsf = nullptr;
+  float* af = nullptr;
+  float* partf = nullptr;
   double* part = nullptr;
   double* erow = nullptr;
   double* apart = nullptr;
@@ -398,6 +402,7 @@ int prepare_system(vgtb_ctx* ctx, int si, const vgtb_system& s, HostSys& h, DevS
     d.wkf = pwf;
   }
   TRY(dalloc(ctx, &d.obs0, 5 * (size_t)h.n_tgt));
+  if (ctx->split) TRY(dalloc(ctx, &d.obs0a, 5 * (size_t)h.nat));
   const size_t NN = (size_t)h.Np * h.Np;
   TRY(dalloc(ctx, &h.Sinv, NN * h.nk));
   TRY(dalloc(ctx, &h.D0, NN * h.nk));
@@ -637,7 +642,7 @@ int finish_density(vgtb_ctx* ctx, int si) {
   HostSys& h = ctx->sys[si];
   const size_t NN = (size_t)h.Np * h.Np;
   for (int k = 0; k < h.nk; ++k) launch_hermitize(h.D0 + k * NN, h.N, h.Np, ctx->stream);
-  if (ctx->delta) launch_obs0(ctx->d_sys, si, h.n_tgt, ctx->stream);
+  if (ctx->delta) launch_obs0(ctx->d_sys, si, h.n_tgt, h.nat, ctx->split ? 1 : 0, ctx->stream);
   CK(cudaGetLastError());
   std::vector<double> q;
   TRY(host_charges(ctx, si, h.D0, q));
@@ -739,6 +744,10 @@ int upload_traj_table(vgtb_ctx* ctx) {
     d.dq = h.dq;
     d.eps = h.eps;
     d.eps_lv = h.eps_lv;
+    d.epsf = h.epsf;
+    d.depsf = h.depsf;
+    d.af = h.af;
+    d.partf = h.partf;
     d.part = h.part;
     d.erow = h.erow;
     d.apart = h.apart;
@@ -988,6 +997,7 @@ void vgtb_default_options(vgtb_options* opt) {
   opt->integrator = VGTB_LEAPFROG;
   opt->cn_iter = 12;
   opt->cn_tol = 1e-10;
+  opt->tile_variant[0] = opt->tile_variant[1] = -1;
 }
 
 int vgtb_create(vgtb_ctx** out, const vgtb_system* sys, const vgtb_options* opt) {
@@ -1028,6 +1038,9 @@ int vgtb_create_batch(vgtb_ctx** out, int n_sys, const vgtb_system* sys, int n_t
   ctx->delta = ctx->split || (ctx->opt.delta_form != 0 && !ctx->cn);
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return bail(fail(ctx, VGTB_E_CUDA, "no CUDA device"));
+  for (int p = 0; p < 2; ++p)
+    if (ctx->opt.tile_variant[p] < -1 || ctx->opt.tile_variant[p] >= tc_num_variants())
+      return bail(fail(ctx, VGTB_E_INVALID, "tile_variant[%d] = %d out of range", p, ctx->opt.tile_variant[p]));
   if (ctx->split && !tc_gemm_supported())
     return bail(fail(ctx, VGTB_E_UNSUPPORTED, "split precision needs an sm_103a (GB300) device"));
   if (ctx->opt.cuda_stream) {
@@ -1124,6 +1137,12 @@ int vgtb_create_batch(vgtb_ctx** out, int n_sys, const vgtb_system* sys, int n_t
     if ((rc = dalloc(ctx, &T.dq, h.nat))) return bail(rc);
     if ((rc = dalloc(ctx, &T.eps, h.nat))) return bail(rc);
     if (ctx->cn && (rc = dalloc(ctx, &T.eps_lv, 2 * (size_t)h.nat))) return bail(rc);
+    if (ctx->split) {
+      if ((rc = dalloc(ctx, &T.epsf, h.nat))) return bail(rc);
+      if ((rc = dalloc(ctx, &T.depsf, h.nat))) return bail(rc);
+      if ((rc = dalloc(ctx, &T.af, 3))) return bail(rc);
+      if ((rc = dalloc(ctx, &T.partf, 5 * (size_t)h.n_tgt))) return bail(rc);
+    }
     if ((rc = dalloc(ctx, &T.part, 5 * (size_t)h.n_tgt))) return bail(rc);
     if ((rc = dalloc(ctx, &T.erow, h.nat))) return bail(rc);
     if ((rc = dalloc(ctx, &T.apart, 4 * (size_t)h.nat))) return bail(rc);
@@ -1206,8 +1225,8 @@ int vgtb_create_batch(vgtb_ctx** out, int n_sys, const vgtb_system* sys, int n_t
       views[s].Wemb_p = fam[s].Wemb;
     }
     std::string msg;
-    if (tc_build_plans(views, ctx->items_h, ctx->opt.timeout_ns, ctx->opt.autotune, -1, ctx->stream, &ctx->tc1,
-                       &ctx->tc2, &msg))
+    if (tc_build_plans(views, ctx->items_h, ctx->opt.timeout_ns, ctx->opt.autotune, ctx->opt.tile_variant, ctx->stream,
+                       &ctx->tc1, &ctx->tc2, &msg))
       return bail(fail(ctx, VGTB_E_CUDA, "tcgen05 plan: %s", msg.c_str()));
   }
   if (ctx->opt.init == VGTB_INIT_GROUND) {

@@ -88,7 +88,8 @@ extern "C" int vgtb_diag_split_chain_variant(int n, const double* a, const doubl
   items[0].Xf = xf;
   TcPlan *p1 = nullptr, *p2 = nullptr;
   std::string msg;
-  if (tc_build_plans(views, items, 2000000000LL, 0, variant, st, &p1, &p2, &msg)) return VGTB_E_CUDA;
+  const int force[2] = {variant, variant};
+  if (tc_build_plans(views, items, 2000000000LL, 0, force, st, &p1, &p2, &msg)) return VGTB_E_CUDA;
   int rc = VGTB_OK;
   if (tc_launch(p1, st) || tc_launch(p2, st)) rc = VGTB_E_CUDA;
   if (cudaDeviceSynchronize() != cudaSuccess) rc = VGTB_E_CUDA;

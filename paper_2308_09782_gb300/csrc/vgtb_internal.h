@@ -111,6 +111,7 @@ struct DevSys {
   double2* kP;             // [3][nk][n_el] momentum P_k = sum e^{-ik.L} i dS/dR_J (Eq. 12)
   double2* kH0;            // [nk][n_el] H0_k
   double* obs0;            // [n_tgt][5] delta forms: the D0 part of the k_obs sums
+  double* obs0a;           // [nat][5] split form: obs0 summed over the targets of each row atom
   double2* Sinv;           // [nk][Np*Np]
   double2* D0;             // [nk][Np*Np]
   double2* R0;             // [nk][Np*Np] (delta forms), else null
@@ -140,6 +141,11 @@ struct DevTraj {
   double* dq;              // [nat] current dq
   double* eps;             // [nat] current eps
   double* eps_lv;          // [2][nat] eps of the two latest levels by parity (Crank-Nicolson), or null
+  // split form: FP32 operands of the phase build, written by k_scc_eps at level n
+  float* epsf;             // [nat] eps_I
+  float* depsf;            // [nat] eps_I - eps0_I
+  float* af;               // [3] A(t_n) / c
+  float* partf;            // [n_tgt][5] split form: FP32 dD parts of the k_obs sums (weighted by w_k)
   double* part;            // [n_tgt][5] per-target partial sums
   double* erow;            // [nat] dq_I eps_I (energy of the SCC term, per row)
   double* apart;           // [nat][4] per-atom shares of T_x, T_y, T_z and the band energy
@@ -196,7 +202,7 @@ void launch_phase(const DevSys* sys, const DevTraj* trj, const DevItem* items, c
                   int n_traj, int total_warps, const int* step, int mode, int fixed_step, cudaStream_t st);
 int scc_configure(int max_nat);
 void launch_kblocks(const DevSys* sys, int s_idx, int n_tgt, int k, cudaStream_t st);
-void launch_obs0(const DevSys* sys, int s_idx, int n_tgt, cudaStream_t st);
+void launch_obs0(const DevSys* sys, int s_idx, int n_tgt, int nat, int split, cudaStream_t st);
 void launch_bloch_setup(const DevSys* sys, int s_idx, int n_tgt, int k, int mode, const double* eps,
                         double2* out, cudaStream_t st);
 void launch_mulliken_setup(const DevSys* sys, int s_idx, int n_tgt, const double2* D, double* part,

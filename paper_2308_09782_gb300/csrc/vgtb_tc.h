@@ -24,11 +24,12 @@ struct TcSysView {
 // Plans for the two products of the split form, over every item:
 //   product 1: W = [dD | D0] [H | dH]^dagger  -> embedded BF16 hi/lo pieces of W
 //   product 2: X = S^-1 W^dagger               -> FP32 planar X
-// force_variant >= 0 uses that tile variant for both; otherwise variant 0, or
-// with autotune the fastest candidate (median of 9 timed launches) per product.
+// force_variant[p] >= 0 uses that tile variant for product p+1; otherwise variant
+// 0, or with autotune the fastest candidate (median of 9 timed launches).
 // Returns 0 on success, else fills *msg.
 int tc_build_plans(const std::vector<TcSysView>& sys, const std::vector<DevItem>& items, long long timeout_ns,
-                   int autotune, int force_variant, cudaStream_t st, TcPlan** p1, TcPlan** p2, std::string* msg);
+                   int autotune, const int force_variant[2], cudaStream_t st, TcPlan** p1, TcPlan** p2,
+                   std::string* msg);
 int tc_num_variants();
 // {tile width, pipeline stages, schedule (0 classic, 1 stream-K, 2 classic waves + stream-K rest), 2-SM pair}
 int tc_variant_info(int v, int* out4);

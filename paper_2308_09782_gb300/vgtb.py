@@ -51,7 +51,8 @@ class VgtbOptions(C.Structure):
                 ("cuda_stream", C.c_void_p), ("timeout_ns", C.c_longlong),
                 ("obs_stride", C.c_int), ("graph_steps", C.c_int), ("autotune", C.c_int),
                 ("scc_tol", C.c_double), ("scc_max_iter", C.c_int),
-                ("integrator", C.c_int), ("cn_iter", C.c_int), ("cn_tol", C.c_double)]
+                ("integrator", C.c_int), ("cn_iter", C.c_int), ("cn_tol", C.c_double),
+                ("tile_variant", C.c_int * 2)]
 
 
 _lib = None
@@ -160,7 +161,10 @@ def default_options(**kw) -> VgtbOptions:
     for k, v in kw.items():
         if not hasattr(o, k):
             raise KeyError(k)
-        setattr(o, k, v)
+        if k == "tile_variant":
+            o.tile_variant[0], o.tile_variant[1] = int(v[0]), int(v[1])
+        else:
+            setattr(o, k, v)
     return o
 
 

@@ -53,6 +53,7 @@ def test_struct_layout_matches_header(lib):
     assert abs(o.scc_tol - 1e-11) < 1e-25 and o.timeout_ns == 2_000_000_000
     # the trailing fields: a layout mismatch would misplace these
     assert o.integrator == vgtb.LEAPFROG and o.cn_iter == 12 and abs(o.cn_tol - 1e-10) < 1e-24
+    assert list(o.tile_variant) == [-1, -1]
 
 
 def test_destroy_is_null_safe(lib):
