@@ -236,7 +236,7 @@ void launch_leap(const LeapItem* items, int n_items, int Np_max, int x_f32, cons
 // pieces of the new level (A operand of the next first product) are split
 // from its FP32 rounding.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_leap_split(const LeapItem* __restrict__ items, const int* step, double dt,
+__global__ void __launch_bounds__(256, 5) k_leap_split(const LeapItem* __restrict__ items, const int* step, double dt,
                                                     int* counter, int* step_rw) {
   pdl_wait();
   pdl_trigger();

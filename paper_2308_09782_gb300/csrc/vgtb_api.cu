@@ -70,9 +70,8 @@ struct HostTraj {
   float* epsf = nullptr;
   float* depsf = nullptr;
   float* af = nullptr;
-  float* partf = nullptr;
   double* part = nullptr;
-  double* erow = nullptr;
+  double* cpart = nullptr;
   double* apart = nullptr;
   int* ticket = nullptr;
   int* status = nullptr;
@@ -328,6 +327,7 @@ int prepare_system(vgtb_ctx* ctx, int si, const vgtb_system& s, HostSys& h, DevS
   d.n_tgt = h.n_tgt;
   d.n_blk = h.n_blk;
   d.omega = h.omega;
+  d.inv_omega = 1.0 / h.omega;
   d.nel = h.nel;
   d.dt = h.dt;
   int* pi;
@@ -390,6 +390,18 @@ int prepare_system(vgtb_ctx* ctx, int si, const vgtb_system& s, HostSys& h, DevS
   d.atom_tgt0 = pi;
   TRY(upload(ctx, &pi, h.tgt_el0.data(), h.tgt_el0.size()));
   d.tgt_el0 = pi;
+  {
+    // vector phase build: 4 columns, column offset and every image's values 16-byte aligned
+    std::vector<int> vec(h.n_tgt, 0);
+    for (int tg = 0; tg < h.n_tgt; ++tg) {
+      const int J = h.tgt_J[tg];
+      bool ok = (h.orb_off[J + 1] - h.orb_off[J]) == 4 && (h.orb_off[J] % 4) == 0 && (tot % 4) == 0;
+      for (int g = h.tgt_img0[tg]; ok && g < h.tgt_img0[tg + 1]; ++g) ok = (h.blk_off[h.img_blk[g]] % 4) == 0;
+      vec[tg] = ok ? 1 : 0;
+    }
+    TRY(upload(ctx, &pi, vec.data(), vec.size()));
+    d.tgt_vec = pi;
+  }
   d.n_el = h.n_el;
   TRY(dalloc(ctx, &d.kS, (size_t)h.nk * h.n_el));
   TRY(dalloc(ctx, &d.kH0, (size_t)h.nk * h.n_el));
@@ -747,9 +759,8 @@ int upload_traj_table(vgtb_ctx* ctx) {
     d.epsf = h.epsf;
     d.depsf = h.depsf;
     d.af = h.af;
-    d.partf = h.partf;
     d.part = h.part;
-    d.erow = h.erow;
+    d.cpart = h.cpart;
     d.apart = h.apart;
     d.ticket = h.ticket;
     d.status = h.status;
@@ -851,7 +862,7 @@ int enqueue_step_cn(vgtb_ctx* ctx, cudaEvent_t* ev, unsigned evflag) {
   launch_gemm_f64(ctx->d_gD, ctx->n_items, ctx->max_Np, ctx->max_Np, nullptr, st);
   launch_obs(ctx->d_sys, ctx->d_trj, ctx->d_items, ctx->d_wpre, nt, ctx->total_warps, ctx->d_step, 0, -1, st);
   if (ev) CK(cudaEventRecordWithFlags(ev[1], st, evflag));
-  launch_scc(ctx->d_sys, ctx->d_trj, nt, ctx->d_step, stride, -1, 1, ctx->max_nat, st);
+  launch_scc(ctx->d_sys, ctx->d_trj, nt, ctx->d_step, stride, -1, 1, ctx->max_nat, 0, st);
   if (ev) CK(cudaEventRecordWithFlags(ev[2], st, evflag));
   launch_phase(ctx->d_sys, ctx->d_trj, ctx->d_items, ctx->d_wpre, nt, ctx->total_warps, ctx->d_step, PH_FP64_CN, -1,
                st);
@@ -868,7 +879,19 @@ int enqueue_step_cn(vgtb_ctx* ctx, cudaEvent_t* ev, unsigned evflag) {
   return VGTB_OK;
 }
 
-int obs_mode(const vgtb_ctx* ctx) { return ctx->split ? 2 : (ctx->delta ? 1 : 0); }
+// observables and SCC of the current level: split form k_obs_atoms_split + k_scc_eps,
+// FP64 paths k_obs + k_scc_atoms + k_scc_eps
+void launch_obs_scc(vgtb_ctx* ctx, cudaEvent_t* ev, unsigned evflag, int stride) {
+  cudaStream_t st = ctx->stream;
+  const int nt = (int)ctx->trj.size();
+  if (ctx->split)
+    launch_obs_atoms_split(ctx->d_sys, ctx->d_trj, ctx->d_items, nt, ctx->max_nat, ctx->d_step, stride, -1, 1, st);
+  else
+    launch_obs(ctx->d_sys, ctx->d_trj, ctx->d_items, ctx->d_wpre, nt, ctx->total_warps, ctx->d_step,
+               ctx->delta ? 1 : 0, -1, st);
+  if (ev) cudaEventRecordWithFlags(ev[1], st, evflag);
+  launch_scc(ctx->d_sys, ctx->d_trj, nt, ctx->d_step, stride, -1, 1, ctx->max_nat, ctx->split ? 1 : 0, st);
+}
 
 int enqueue_step(vgtb_ctx* ctx, cudaEvent_t* ev) {
   cudaStream_t st = ctx->stream;
@@ -882,10 +905,7 @@ int enqueue_step(vgtb_ctx* ctx, cudaEvent_t* ev) {
   const int stride = ctx->opt.obs_stride > 0 ? ctx->opt.obs_stride : 1;
   if (ev) CK(cudaEventRecordWithFlags(ev[0], st, evflag));
   if (ctx->cn) return enqueue_step_cn(ctx, ev, evflag);
-  launch_obs(ctx->d_sys, ctx->d_trj, ctx->d_items, ctx->d_wpre, nt, ctx->total_warps, ctx->d_step, obs_mode(ctx),
-             -1, st);
-  if (ev) CK(cudaEventRecordWithFlags(ev[1], st, evflag));
-  launch_scc(ctx->d_sys, ctx->d_trj, nt, ctx->d_step, stride, -1, 1, ctx->max_nat, st);
+  launch_obs_scc(ctx, ev, evflag, stride);
   if (ev) CK(cudaEventRecordWithFlags(ev[2], st, evflag));
   if (ctx->split)
     launch_phase_split(ctx->d_sys, ctx->d_trj, ctx->d_items, ctx->d_wpre, nt, ctx->total_warps, ctx->d_step, st);
@@ -1141,10 +1161,9 @@ int vgtb_create_batch(vgtb_ctx** out, int n_sys, const vgtb_system* sys, int n_t
       if ((rc = dalloc(ctx, &T.epsf, h.nat))) return bail(rc);
       if ((rc = dalloc(ctx, &T.depsf, h.nat))) return bail(rc);
       if ((rc = dalloc(ctx, &T.af, 3))) return bail(rc);
-      if ((rc = dalloc(ctx, &T.partf, 5 * (size_t)h.n_tgt))) return bail(rc);
     }
     if ((rc = dalloc(ctx, &T.part, 5 * (size_t)h.n_tgt))) return bail(rc);
-    if ((rc = dalloc(ctx, &T.erow, h.nat))) return bail(rc);
+    if ((rc = dalloc(ctx, &T.cpart, 6 * (size_t)((h.nat + kSccRowsPerCta - 1) / kSccRowsPerCta)))) return bail(rc);
     if ((rc = dalloc(ctx, &T.apart, 4 * (size_t)h.nat))) return bail(rc);
     if ((rc = dalloc(ctx, &T.ticket, 1))) return bail(rc);
     if ((rc = dalloc(ctx, &T.status, 1))) return bail(rc);
@@ -1379,9 +1398,13 @@ int vgtb_propagate(vgtb_ctx* ctx, int nsteps) {
   // observables of the final level
   const int nt = (int)ctx->trj.size();
   if (ctx->cn) launch_gemm_f64(ctx->d_gD, ctx->n_items, ctx->max_Np, ctx->max_Np, nullptr, ctx->stream);
-  launch_obs(ctx->d_sys, ctx->d_trj, ctx->d_items, ctx->d_wpre, nt, ctx->total_warps, ctx->d_step, obs_mode(ctx),
-             -1, ctx->stream);
-  launch_scc(ctx->d_sys, ctx->d_trj, nt, ctx->d_step, ctx->opt.obs_stride, -1, 1, ctx->max_nat, ctx->stream);
+  if (ctx->cn) {
+    launch_obs(ctx->d_sys, ctx->d_trj, ctx->d_items, ctx->d_wpre, nt, ctx->total_warps, ctx->d_step, 0, -1,
+               ctx->stream);
+    launch_scc(ctx->d_sys, ctx->d_trj, nt, ctx->d_step, ctx->opt.obs_stride, -1, 1, ctx->max_nat, 0, ctx->stream);
+  } else {
+    launch_obs_scc(ctx, nullptr, 0, ctx->opt.obs_stride);
+  }
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(ctx->stream));
   ctx->n_done += nsteps;

@@ -86,9 +86,12 @@ __device__ __forceinline__ float d2f_bits(double d) {
   return __uint_as_float(f);
 }
 
+constexpr int kSccRowsPerCta = 4;  // rows of gamma per CTA of k_scc_eps (one warp each)
+
 struct DevSys {
   int N, Np, nat, nk, n_tgt, n_blk;
   double omega, nel, dt;
+  double inv_omega;        // 1 / omega (an FP64 division is a long sequence on GB300)
   const int* orb_off;      // [nat+1]
   const double* z;         // [nat]
   const double* gamma;     // [nat*nat]
@@ -107,6 +110,7 @@ struct DevSys {
   const int* atom_tgt0;    // [nat+1] targets of row atom I are atom_tgt0[I]..atom_tgt0[I+1]-1
   int n_el;                // elements over all targets (sum of n_I n_J)
   const int* tgt_el0;      // [n_tgt+1] first element of each target
+  const int* tgt_vec;      // [n_tgt] 1: 4-column blocks with 16-byte aligned values (vector phase build)
   double2* kS;             // [nk][n_el] Bloch-summed S_k at the target elements (Eq. 7)
   double2* kP;             // [3][nk][n_el] momentum P_k = sum e^{-ik.L} i dS/dR_J (Eq. 12)
   double2* kH0;            // [nk][n_el] H0_k
@@ -145,9 +149,8 @@ struct DevTraj {
   float* epsf;             // [nat] eps_I
   float* depsf;            // [nat] eps_I - eps0_I
   float* af;               // [3] A(t_n) / c
-  float* partf;            // [n_tgt][5] split form: FP32 dD parts of the k_obs sums (weighted by w_k)
   double* part;            // [n_tgt][5] per-target partial sums
-  double* erow;            // [nat] dq_I eps_I (energy of the SCC term, per row)
+  double* cpart;           // [ceil(nat / kSccRowsPerCta)][6] per-CTA partial sums of k_scc_eps
   double* apart;           // [nat][4] per-atom shares of T_x, T_y, T_z and the band energy
   int* ticket;             // [1] CTA arrival counter of k_scc (reset by the last CTA)
   int* status;
@@ -188,13 +191,15 @@ enum PhaseMode : int {
 };
 
 // Launchers (all enqueue on `st`)
-// delta: 0 = D itself (FP64), 1 = dD with the D0 part from obs0 (FP64), 2 = the same
-// with the dD sums in FP32 (split form)
+// delta: 0 = D itself (FP64), 1 = dD with the D0 part from obs0 (FP64)
 void launch_obs(const DevSys* sys, const DevTraj* trj, const DevItem* items, const int* warp_prefix,
                 int n_traj, int total_warps, const int* step, int delta, int fixed_step, cudaStream_t st);
 void launch_kblocks_f32(const DevSys* sys, int s_idx, long long n, cudaStream_t st);
+// atoms_done = 1: the per-atom sums were made by k_obs_atoms_split (split form)
 void launch_scc(const DevSys* sys, DevTraj* trj, int n_traj, const int* step, int stride,
-                int fixed_step, int record, int max_nat, cudaStream_t st);
+                int fixed_step, int record, int max_nat, int atoms_done, cudaStream_t st);
+void launch_obs_atoms_split(const DevSys* sys, DevTraj* trj, const DevItem* items, int n_traj, int max_nat,
+                            const int* step, int stride, int fixed_step, int record, cudaStream_t st);
 void launch_phase_split(const DevSys* sys, const DevTraj* trj, const DevItem* items, const int* warp_prefix,
                         int n_traj, int total_units, const int* step, cudaStream_t st);
 void launch_to_planar_f32(const double2* src, float* dst, int Np, cudaStream_t st);

@@ -248,6 +248,40 @@ def kick_field(nsteps: int, a0: float, pol=(1.0, 0.0, 0.0)) -> np.ndarray:
     return np.tile(a0 * pol, (nsteps + 1, 1))
 
 
+BOHR_PER_ANGSTROM = 1.0 / 0.529177210903
+HARTREE_EV = 27.211386245988
+AU_TIME_FS = 0.0241888432658
+
+
+def coordination_numbers(sysd: dict, r_bond: float = 2.85 * BOHR_PER_ANGSTROM) -> np.ndarray:
+    """Neighbours of each atom within r_bond (bohr; 2.85 A is the bond-length cut-off
+    of the a-Si coordination analysis in Sec. 3.3), over all periodic images."""
+    lat = np.asarray(sysd["lattice"], float)
+    pos = np.asarray(sysd["pos"], float)
+    n = len(pos)
+    inv = np.linalg.inv(lat)
+    cn = np.zeros(n, dtype=np.int64)
+    reach = [int(np.ceil(r_bond * np.linalg.norm(inv[:, i]))) for i in range(3)]
+    shifts = np.array([(a, b, c) for a in range(-reach[0], reach[0] + 1)
+                       for b in range(-reach[1], reach[1] + 1)
+                       for c in range(-reach[2], reach[2] + 1)], float) @ lat
+    for i in range(n):
+        d = pos[None, :, :] + shifts[:, None, :] - pos[i][None, None, :]
+        r = np.linalg.norm(d, axis=2)
+        cn[i] = int(np.sum((r > 1e-8) & (r <= r_bond)))
+    return cn
+
+
+def laser_sweep(dt: float = 0.2, e0: float = 0.00534, energies_ev=(2.3, 3.9, 6.0), duration_fs: float = 20.0,
+                pol=(1.0, 0.0, 0.0)):
+    """Fields of the laser experiment of Sec. 3.3: a sin^2-enveloped pulse of 20 fs
+    (centred at 10 fs) at each photon energy, E0 = 0.00534 au (10^12 W/cm^2, about
+    0.274 eV/A) along x.  Returns (list of A tables, nsteps)."""
+    T = duration_fs / AU_TIME_FS
+    n = int(round(T / dt))
+    return [pulse_field(n, dt, e0, w / HARTREE_EV, pol=pol, duration=T) for w in energies_ev], n
+
+
 def config(name: str):
     """Named workloads: returns (system, A table, nsteps).
 
