@@ -70,3 +70,32 @@ def test_group_charges_match_oracle_series():
     assert dq.shape == ref.shape
     assert np.abs(dq - ref).max() <= 1e-10
     assert np.abs(ref).max() > 1e-6
+
+
+def test_laser_sweep_coordination_charge_transfer_matches_oracle():
+    """The laser experiment of Sec. 3.3 in small: three photon energies as three
+    trajectories of one context (FP64), charge transfer per coordination class
+    (2.85 A bond cut-off) against the oracle's charges of each single run."""
+    from paper_2308_09782_gb300 import inputs, vgtb
+    sysd = inputs.diamond_si(2, 0.3, seed=64, kgrid="gamma")
+    ctx = O.setup(sysd)
+    gs = O.ground_state(sysd, ctx=ctx)
+    fields, _ = inputs.laser_sweep(sysd["dt"])
+    n = 250
+    cn = inputs.coordination_numbers(sysd)
+    classes = sorted(set(cn.tolist()))
+    assert len(classes) >= 2                          # the displacements break some bonds
+    group = np.array([classes.index(c) for c in cn], np.int32)
+    with vgtb.Context([sysd], traj_sys=[0, 0, 0], init=vgtb.INIT_USER) as c:
+        c.set_density(0, 0, gs["D"][0])
+        for tr, f in enumerate(fields):
+            c.set_field(tr, f[:n + 1])
+        c.propagate(n)
+        got = [c.group_charges(tr, group, len(classes)) for tr in range(3)]
+    moved = []
+    for tr, f in enumerate(fields):
+        q = O.propagate(sysd, f[:n + 1], n, gs["D"], ctx=ctx)["q"]
+        ref = np.stack([-(q[:, group == g] - q[0, group == g]).sum(1) for g in range(len(classes))], 1)
+        assert np.abs(got[tr] - ref).max() <= 1e-10
+        moved.append(np.abs(ref).max())
+    assert min(moved) > 1e-7                          # every pulse moved charge

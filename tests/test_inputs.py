@@ -119,3 +119,42 @@ def test_kpoint_sets(kind, nk):
     # every set is closed under k -> -k modulo reciprocal lattice vectors
     for kk in k:
         assert np.any(np.all(np.abs(((k + kk + 0.5) % 1.0) - 0.5) < 1e-12, axis=1))
+
+
+def test_coordination_numbers():
+    """Diamond: 4 nearest neighbours at a sqrt(3)/4 = 4.44 bohr, the next shell at
+    a/sqrt(2) = 7.26 bohr, so every atom is 4-coordinated with the 2.85 A (5.39 bohr) cut-off,
+    in the cell and in a supercell (periodic images counted).  Pulling one atom 2 bohr away
+    from one neighbour along their bond makes both 3-coordinated."""
+    for n in (1, 2):
+        s = inputs.diamond_si(n, 0.0, seed=0, kgrid="gamma")
+        assert np.all(inputs.coordination_numbers(s) == 4)
+    s = inputs.diamond_si(2, 0.0, seed=0, kgrid="gamma")
+    pos = np.array(s["pos"], float)
+    lat = np.asarray(s["lattice"], float)
+    d = pos - pos[0]
+    d -= np.round(d @ np.linalg.inv(lat)) @ lat
+    r = np.linalg.norm(d, axis=1)
+    j = int(np.argmin(np.where(r > 1e-8, r, np.inf)))
+    pos[0] -= 2.0 * d[j] / r[j]
+    s2 = dict(s)
+    s2["pos"] = pos
+    cn = inputs.coordination_numbers(s2)
+    assert cn[0] == 3 and cn[j] == 3
+    assert np.sum(cn == 4) == len(cn) - 2
+
+
+def test_laser_sweep_fields():
+    """Sec. 3.3: 20 fs sin^2 pulses at 2.3 / 3.9 / 6.0 eV, 10^12 W/cm^2 (E0 = 0.00534 au) along x."""
+    fields, n = inputs.laser_sweep(0.2)
+    assert n == round(20.0 / 0.0241888432658 / 0.2)
+    assert len(fields) == 3
+    for f, ev in zip(fields, (2.3, 3.9, 6.0)):
+        w = ev / 27.211386245988
+        ref = inputs.pulse_field(n, 0.2, 0.00534, w, duration=20.0 / 0.0241888432658)
+        assert np.allclose(f, ref, rtol=0, atol=1e-12)
+        assert np.all(f[:, 1:] == 0.0)
+    # the field's intensity: I = (c / 8 pi) E0^2 in atomic units -> W/cm^2
+    e0_au = 0.00534
+    i_wcm2 = 3.50944758e16 * e0_au ** 2
+    assert abs(i_wcm2 / 1e12 - 1.0) < 0.01
