@@ -48,6 +48,8 @@ def parse():
     p.add_argument("--cpu-steps", type=int, default=6)
     p.add_argument("--tiles", default="auto",
                    help="tcgen05 tile variants of product 1,2 (e.g. 1,0) instead of the autotuner's choice")
+    p.add_argument("--laser-steps", type=int, default=0,
+                   help="laser workload: steps to run (0 = the whole 20 fs pulse)")
     p.add_argument("--cn-steps", type=int, default=4,
                    help="timed steps of the FP64 Crank-Nicolson integrator (0 = skip)")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -494,7 +496,7 @@ def laser(args):
     vgtb.load()
     sysd, _, _ = inputs.config(CONFIG)
     fields, n = inputs.laser_sweep(sysd["dt"])
-    K = n if args.steps >= n else args.steps
+    K = n if args.laser_steps <= 0 else min(args.laser_steps, n)
     cn = inputs.coordination_numbers(sysd)
     classes = sorted(set(cn.tolist()))
     group = np.array([classes.index(c) for c in cn], np.int32)

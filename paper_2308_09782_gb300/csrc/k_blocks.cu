@@ -238,26 +238,33 @@ __device__ __forceinline__ float half_sum_f(float v) {
 
 // ---------------------------------------------------------------------------
 // k_obs_atoms_split: the split form's observables and per-atom sums in one
-// launch.  One CTA per (trajectory, atom I); its half-warps take the targets
-// (I, J) of the atom and form the dD sums in FP32 (dD converted from the FP64
-// master with integer operations, k-space blocks as packed FP32 records); warp
-// 0 adds the 32 half-warp sums in FP64, then the constant D0 part (obs0a) and
-// the A terms (both linear in the sums) and writes dq_I, q_I and the atom's
-// shares of T and of the band energy, as k_scc_atoms does for the FP64 paths.
-// GB300 issues an FP64 warp instruction at a small fraction of the FP32 rate,
-// whatever the number of active lanes, so FP64 stays in warp 0.  The FP32
-// rounding of the dD part is far below the BF16x3 products' own error.
+// launch.  One CTA per (trajectory, atom I); its threads take the nonzeros of
+// the atom's rows (all targets (I, J)) and form the dD sums in FP32 (dD
+// converted from the FP64 master with integer operations, k-space blocks as
+// packed FP32 records); warp 0 adds the 16 warp sums in FP64, then the
+// constant D0 part (obs0a) and the A terms (both linear in the sums) and writes
+// dq_I, q_I and the atom's shares of T and of the band energy, as k_scc_atoms
+// does for the FP64 paths.  GB300 issues an FP64 warp instruction at a small
+// fraction of the FP32 rate, whatever the number of active lanes, so FP64 stays
+// in warp 0.  The FP32 rounding of the dD part is far below the BF16x3
+// products' own error.
 // ---------------------------------------------------------------------------
-constexpr int kObsAtomThreads = 512;  // 32 half-warps: one pass over the ~29 targets of an atom
-constexpr int kObsHalfWarps = kObsAtomThreads / 16;
+constexpr int kObsAtomThreads = 512;  // one pass over the ~464 nonzeros of an sp3 atom's row block
+
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
 
 __global__ void __launch_bounds__(kObsAtomThreads) k_obs_atoms_split(const DevSys* __restrict__ sysv, DevTraj* trj,
-                                                         const DevItem* __restrict__ items, int n_traj, int max_nat,
-                                                         const int* __restrict__ step, int stride, int fixed_step,
-                                                         int record) {
+                                                                   const DevItem* __restrict__ items, int n_traj,
+                                                                   int max_nat, const int* __restrict__ step,
+                                                                   int stride, int fixed_step, int record) {
   pdl_wait();
   pdl_trigger();
-  __shared__ float red[5][kObsHalfWarps];
+  constexpr int NW = kObsAtomThreads / 32;
+  __shared__ float red[5][NW];
   const int t = blockIdx.x / max_nat, I = blockIdx.x % max_nat;
   if (t >= n_traj) return;
   DevTraj& T = trj[t];
@@ -265,54 +272,44 @@ __global__ void __launch_bounds__(kObsAtomThreads) k_obs_atoms_split(const DevSy
   if (I >= S.nat) return;
   const int n = fixed_step >= 0 ? fixed_step : *step;
   const int par = n & 1;
-  const int hw = threadIdx.x >> 4, lane = threadIdx.x & 15;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float sS = 0.f, sx = 0.f, sy = 0.f, sz = 0.f, sH = 0.f;
-  const int oi = S.orb_off[I];
-  for (int tg = S.atom_tgt0[I] + hw; tg < S.atom_tgt0[I + 1]; tg += kObsHalfWarps) {
-    const int J = S.tgt_J[tg];
-    const int oj = S.orb_off[J], nj = S.orb_off[J + 1] - oj;
-    const int el0 = S.tgt_el0[tg], nel = S.tgt_el0[tg + 1] - el0;
+  // the atom's nonzeros are contiguous (targets sorted by row atom); el_off gives
+  // each one's offset in the Np x Np matrix, so a thread needs no index lookups
+  const int e0 = S.el_atom0[I], e1 = S.el_atom0[I + 1];
+  for (int e = e0 + threadIdx.x; e < e1; e += kObsAtomThreads) {
+    const long long off = S.el_off[e];
     for (int k = 0; k < S.nk; ++k) {
-      const double2* Dk = items[T.item0 + k].D[par];
-      const float4* kb = S.kf + 3 * ((long long)k * S.n_el + el0);
-      float lS = 0.f, lx = 0.f, ly = 0.f, lz = 0.f, lH = 0.f;
-      for (int e = lane; e < nel; e += 16) {
-        const int a = e / nj, b = e - a * nj;
-        const double2 dd = Dk[(long long)(oi + a) * S.Np + (oj + b)];
-        const float dr = d2f_bits(dd.x), di = d2f_bits(dd.y);
-        const float4 c0 = kb[3 * e], c1 = kb[3 * e + 1], c2 = kb[3 * e + 2];
-        lS = fmaf(dr, c0.x, fmaf(di, c0.y, lS));
-        lx = fmaf(dr, c0.z, fmaf(di, c0.w, lx));
-        ly = fmaf(dr, c1.x, fmaf(di, c1.y, ly));
-        lz = fmaf(dr, c1.z, fmaf(di, c1.w, lz));
-        lH = fmaf(dr, c2.x, fmaf(di, c2.y, lH));
-      }
+      const double2 dd = items[T.item0 + k].D[par][off];
+      const float4* kb = S.kf + 3 * ((long long)k * S.n_el + e);
+      const float4 c0 = kb[0], c1 = kb[1], c2 = kb[2];
+      const float dr = d2f_bits(dd.x), di = d2f_bits(dd.y);
       const float wk = S.wkf[k];
-      sS = fmaf(wk, lS, sS);
-      sx = fmaf(wk, lx, sx);
-      sy = fmaf(wk, ly, sy);
-      sz = fmaf(wk, lz, sz);
-      sH = fmaf(wk, lH, sH);
+      sS = fmaf(wk, fmaf(dr, c0.x, di * c0.y), sS);
+      sx = fmaf(wk, fmaf(dr, c0.z, di * c0.w), sx);
+      sy = fmaf(wk, fmaf(dr, c1.x, di * c1.y), sy);
+      sz = fmaf(wk, fmaf(dr, c1.z, di * c1.w), sz);
+      sH = fmaf(wk, fmaf(dr, c2.x, di * c2.y), sH);
     }
   }
-  sS = half_sum_f(sS);
-  sx = half_sum_f(sx);
-  sy = half_sum_f(sy);
-  sz = half_sum_f(sz);
-  sH = half_sum_f(sH);
+  sS = warp_sum_f(sS);
+  sx = warp_sum_f(sx);
+  sy = warp_sum_f(sy);
+  sz = warp_sum_f(sz);
+  sH = warp_sum_f(sH);
   if (lane == 0) {
-    red[0][hw] = sS;
-    red[1][hw] = sx;
-    red[2][hw] = sy;
-    red[3][hw] = sz;
-    red[4][hw] = sH;
+    red[0][warp] = sS;
+    red[1][warp] = sx;
+    red[2][warp] = sy;
+    red[3][warp] = sz;
+    red[4][warp] = sH;
   }
   __syncthreads();
   if (threadIdx.x >= 32) return;
   const int l = threadIdx.x;
   double v[5];
 #pragma unroll
-  for (int i = 0; i < 5; ++i) v[i] = warp_sum(f2d_bits(red[i][l]));
+  for (int i = 0; i < 5; ++i) v[i] = warp_sum(l < NW ? f2d_bits(red[i][l]) : 0.0);
   if (l != 0) return;
   const double* o = S.obs0a + 5LL * I;
 #pragma unroll

@@ -401,6 +401,22 @@ int prepare_system(vgtb_ctx* ctx, int si, const vgtb_system& s, HostSys& h, DevS
     }
     TRY(upload(ctx, &pi, vec.data(), vec.size()));
     d.tgt_vec = pi;
+    // element offsets of the nonzeros (row-major within each target) and per-atom ranges
+    if ((long long)h.Np * h.Np > 2147483647LL) return fail(ctx, VGTB_E_INVALID, "system %d: Np too large", si);
+    std::vector<int> eoff(h.n_el), eat(h.nat + 1);
+    for (int tg = 0; tg < h.n_tgt; ++tg) {
+      const int oi = h.orb_off[h.tgt_I[tg]], oj = h.orb_off[h.tgt_J[tg]];
+      const int nj = h.orb_off[h.tgt_J[tg] + 1] - oj;
+      for (int e = h.tgt_el0[tg]; e < h.tgt_el0[tg + 1]; ++e) {
+        const int a = (e - h.tgt_el0[tg]) / nj, b = (e - h.tgt_el0[tg]) % nj;
+        eoff[e] = (oi + a) * h.Np + oj + b;
+      }
+    }
+    for (int i = 0; i <= h.nat; ++i) eat[i] = h.tgt_el0[h.atom_tgt0[i]];
+    TRY(upload(ctx, &pi, eoff.data(), eoff.size()));
+    d.el_off = pi;
+    TRY(upload(ctx, &pi, eat.data(), eat.size()));
+    d.el_atom0 = pi;
   }
   d.n_el = h.n_el;
   TRY(dalloc(ctx, &d.kS, (size_t)h.nk * h.n_el));

@@ -111,6 +111,8 @@ struct DevSys {
   int n_el;                // elements over all targets (sum of n_I n_J)
   const int* tgt_el0;      // [n_tgt+1] first element of each target
   const int* tgt_vec;      // [n_tgt] 1: 4-column blocks with 16-byte aligned values (vector phase build)
+  const int* el_off;       // [n_el] offset (row * Np + column) of each nonzero in an Np x Np matrix
+  const int* el_atom0;     // [nat+1] first nonzero of each row atom (= tgt_el0[atom_tgt0[I]])
   double2* kS;             // [nk][n_el] Bloch-summed S_k at the target elements (Eq. 7)
   double2* kP;             // [3][nk][n_el] momentum P_k = sum e^{-ik.L} i dS/dR_J (Eq. 12)
   double2* kH0;            // [nk][n_el] H0_k
