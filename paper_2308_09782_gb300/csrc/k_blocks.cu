@@ -241,7 +241,7 @@ __device__ __forceinline__ float half_sum_f(float v) {
 // launch.  One CTA per (trajectory, atom I); its threads take the nonzeros of
 // the atom's rows (all targets (I, J)) and form the dD sums in FP32 (dD
 // converted from the FP64 master with integer operations, k-space blocks as
-// packed FP32 records); warp 0 adds the 16 warp sums in FP64, then the
+// packed FP32 records); warp 0 adds the 8 warp sums in FP64, then the
 // constant D0 part (obs0a) and the A terms (both linear in the sums) and writes
 // dq_I, q_I and the atom's shares of T and of the band energy, as k_scc_atoms
 // does for the FP64 paths.  GB300 issues an FP64 warp instruction at a small
@@ -249,7 +249,9 @@ __device__ __forceinline__ float half_sum_f(float v) {
 // in warp 0.  The FP32 rounding of the dD part is far below the BF16x3
 // products' own error.
 // ---------------------------------------------------------------------------
-constexpr int kObsAtomThreads = 512;  // one pass over the ~464 nonzeros of an sp3 atom's row block
+// 256 threads: two passes over the ~464 nonzeros of an sp3 atom's row block, and
+// every CTA of a 512-atom step resident in one wave (512 threads took 1.1 waves)
+constexpr int kObsAtomThreads = 256;
 
 __device__ __forceinline__ float warp_sum_f(float v) {
 #pragma unroll
@@ -429,16 +431,25 @@ __global__ void __launch_bounds__(kSccThreads) k_scc_eps(const DevSys* __restric
   if (I < S.nat) {
     const double* g = S.gamma + (long long)I * S.nat;
     const double* dq = T.dq;
-    // four independent partial sums keep four loads in flight per lane
+    // chunks of 512 columns: all 16 loads of a lane are issued before the first
+    // FMA, so a chunk costs one memory latency; four partial sums
     double e0 = 0.0, e1 = 0.0, e2 = 0.0, e3 = 0.0;
-    int K = lane;
-    for (; K + 96 < S.nat; K += 128) {
-      e0 += g[K] * dq[K];
-      e1 += g[K + 32] * dq[K + 32];
-      e2 += g[K + 64] * dq[K + 64];
-      e3 += g[K + 96] * dq[K + 96];
+    for (int base = 0; base < S.nat; base += 512) {
+      double gv[16], qv[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int K = base + lane + 32 * j;
+        gv[j] = K < S.nat ? g[K] : 0.0;
+        qv[j] = K < S.nat ? dq[K] : 0.0;
+      }
+#pragma unroll
+      for (int j = 0; j < 16; j += 4) {
+        e0 = fma(gv[j], qv[j], e0);
+        e1 = fma(gv[j + 1], qv[j + 1], e1);
+        e2 = fma(gv[j + 2], qv[j + 2], e2);
+        e3 = fma(gv[j + 3], qv[j + 3], e3);
+      }
     }
-    for (; K < S.nat; K += 32) e0 += g[K] * dq[K];
     const double e = warp_sum((e0 + e1) + (e2 + e3));
     if (lane == 0) {
       T.eps[I] = e;
