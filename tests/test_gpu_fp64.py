@@ -1,6 +1,6 @@
 """Parity of the plain FP64 CUDA path with the CPU oracle (through the C-ABI).
 
-Tolerances (BASELINE target): relative Frobenius error <= 1e-10 in D_k after
+Tolerances: relative Frobenius error <= 1e-10 in D_k after
 the stated step count and <= 1e-8 in J(t) over the whole series.
 """
 import numpy as np

@@ -3,7 +3,7 @@
 tests/golden/si512_kick_oracle.npz is written by tests/golden/make_oracle_reference.py
 (oracle only: SCC ground state, then 5000 leapfrog steps; J and E at every level, q every
 250 steps).  The split form runs all 5000 steps from the library's own ground state
-(BASELINE target: J within 1e-4 of the FP64 oracle); the FP64 path runs 500 steps from
+(J within 1e-4 of the FP64 oracle, the bound of the split-precision form); the FP64 path runs 500 steps from
 the oracle's ground state (target 1e-8 in J).
 """
 import os

@@ -2,7 +2,7 @@
 
 Product-level tolerance: BF16 hi/lo pieces carry ~2^-17 relative precision and
 three partial products are accumulated in FP32, so a relative Frobenius error
-of 3e-5 bounds one product.  Propagation tolerance (BASELINE target): J(t)
+of 3e-5 bounds one product.  Propagation tolerance of the split-precision form: J(t)
 within 1e-4 relative of the FP64 oracle.
 """
 import numpy as np
