@@ -215,8 +215,8 @@ int vgtb_set_state(vgtb_ctx* ctx, const void* buf, long long bytes);
  * Crank-Nicolson contexts use the same classes for: OBS = D = 2 C C^dagger and
  * the sums, GEMM1 = S^-1 H(t+dt/2), GEMM2 = the fixed-point sweeps, LEAP = the
  * convergence check and the step counter. */
-#define VGTB_K_OBS     0   /* charges / current / energy partial sums (Eqs. 10, 14) */
-#define VGTB_K_SCC     1   /* dq, eps = gamma dq, finalised observables */
+#define VGTB_K_OBS     0   /* charges / current / energy sums (Eqs. 10, 14); split form: per atom, with dq */
+#define VGTB_K_SCC     1   /* (FP64 forms: dq), eps = gamma dq, finalised observables */
 #define VGTB_K_PHASE   2   /* Bloch sum of H_k(t) with A(t) (Eqs. 7-12) */
 #define VGTB_K_GEMM1   3   /* first commutator product */
 #define VGTB_K_GEMM2   4   /* second commutator product (S^-1 applied) */
