@@ -64,3 +64,25 @@ def test_fp64_512_kick_500_steps_vs_stored_oracle(gold):
         J, E, _ = c.observables(0)
     assert rel_fro([J], [gold["J"][:m + 1]]) <= 1e-8
     assert np.abs(E - gold["E"][:m + 1]).max() <= 1e-9 * np.abs(gold["E"]).max()
+
+
+@pytest.mark.skipif(os.environ.get("VGTB_FULL_FP64") != "1",
+                    reason="the 5000-step FP64 run takes about ten minutes; set VGTB_FULL_FP64=1 to run it")
+def test_fp64_512_kick_full_run_vs_stored_oracle(gold):
+    """The plain FP64 path over the whole stated run (5000 steps) from the oracle's ground state."""
+    from paper_2308_09782_gb300 import vgtb
+    sysd, A, n = system("si512_kick")
+    ctx = O.setup(sysd)
+    gs = O.ground_state(sysd, ctx=ctx)
+    with vgtb.Context(sysd, precision=vgtb.FP64, init=vgtb.INIT_USER, obs_stride=250) as c:
+        c.set_density(0, 0, gs["D"][0])
+        c.set_field(0, A)
+        c.propagate(n)
+        J, E, q = c.observables(0)
+    err_j = rel_fro([J], [gold["J"]])
+    err_e = np.abs(E - gold["E"]).max() / np.abs(gold["E"]).max()
+    err_q = np.abs(q - gold["q"]).max()
+    print(f"si512_kick FP64, {n} steps: J {err_j:.2e}  E {err_e:.2e}  q {err_q:.2e}")
+    assert err_j <= 1e-8
+    assert err_e <= 1e-9
+    assert err_q <= 1e-10
