@@ -251,14 +251,17 @@ def observables(ctx, D_list, A):
     return J, E, q, eps[ctx["atom_of"]]
 
 
-def propagate(sysd, A_table, nsteps, D0_list, ctx=None, D_prev_list=None, n0=0):
+def propagate(sysd, A_table, nsteps, D0_list, ctx=None, D_prev_list=None, n0=0, eps_fixed=None):
     """Leapfrog propagation of D_k for `nsteps` steps from time level n0.
 
     At every level t_n (n = n0 .. n0+nsteps) the charges, SCC shift, current
     and energy are evaluated from D(t_n); for n < n0+nsteps, dD/dt(t_n) follows
     Eq. 6 with H_k(t_n) and D(t_{n+1}) follows Eq. 13 (forward Euler when no
-    earlier level is given).  Returns dict(J, E, q, D, D_prev) where D is
-    D(t_{n0+nsteps}) and D_prev is D(t_{n0+nsteps-1}).
+    earlier level is given).  With eps_fixed (atom-resolved shifts eps_I), the
+    H2 term of Eq. 10 uses those shifts at every level instead of gamma dq(t_n)
+    (the SCC shift frozen: a non-self-consistent propagation); the charges and
+    the energy are still evaluated from D(t_n).  Returns dict(J, E, q, D,
+    D_prev) where D is D(t_{n0+nsteps}) and D_prev is D(t_{n0+nsteps-1}).
     """
     ctx = setup(sysd) if ctx is None else ctx
     dt = float(sysd["dt"])
@@ -269,6 +272,8 @@ def propagate(sysd, A_table, nsteps, D0_list, ctx=None, D_prev_list=None, n0=0):
     for n in range(n0, n0 + nsteps + 1):
         A = A_table[n]
         J, E, q, eps_orb = observables(ctx, D, A)
+        if eps_fixed is not None:
+            eps_orb = np.asarray(eps_fixed, float)[ctx["atom_of"]]
         Js.append(J)
         Es.append(E)
         qs.append(q)

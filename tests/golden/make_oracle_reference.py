@@ -5,8 +5,12 @@ Calls only ``oracle/`` and the seeded input generator.  Usage:
     python tests/golden/make_oracle_reference.py si512_kick [nsteps]
 
 writes ``tests/golden/<config>_oracle.npz`` with the SCC ground-state charges
-dq0, the current J(t_n) (n = 0..nsteps, 3 components), the energy E(t_n) and
-the Mulliken charges q(t_n) every 250 steps.
+dq0, the current J(t_n) (n = 0..nsteps, 3 components), the energy E(t_n), the
+Mulliken charges q(t_n) every 250 steps and a record of the final density
+matrix D(t_nsteps) of the first k-point: its diagonal atom blocks (``d_diag``,
+atom by atom, row-major), the entries at a seeded uniform sample of positions
+(``d_rows``, ``d_cols``, ``d_sample``) and its Frobenius norm (``d_fro``).
+The full N x N matrix is too large to store.
 """
 import os
 import sys
@@ -50,9 +54,19 @@ def main():
     E.append(r["E"])
     qs.append(r["q"][0])
     qsteps.append(n)
-    out = os.path.join(HERE, f"{name}_oracle.npz")
+    Df = np.asarray(D[0])
+    off = np.asarray(sysd["orb_offset"])
+    d_diag = np.concatenate([Df[off[i]:off[i + 1], off[i]:off[i + 1]].ravel()
+                             for i in range(len(off) - 1)])
+    rng = np.random.default_rng(20230818)
+    n_orb = Df.shape[0]
+    rows = rng.integers(0, n_orb, size=16384).astype(np.int32)
+    cols = rng.integers(0, n_orb, size=16384).astype(np.int32)
+    out = os.environ.get("VGTB_GOLDEN_OUT") or os.path.join(HERE, f"{name}_oracle.npz")
     np.savez_compressed(out, dq0=gs["dq"], J=np.concatenate(J), E=np.concatenate(E),
-                        q=np.array(qs), q_steps=np.array(qsteps), nsteps=nsteps)
+                        q=np.array(qs), q_steps=np.array(qsteps), nsteps=nsteps,
+                        d_diag=d_diag, d_rows=rows, d_cols=cols, d_sample=Df[rows, cols],
+                        d_fro=np.linalg.norm(Df))
     print("wrote", out)
 
 

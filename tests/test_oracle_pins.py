@@ -126,6 +126,37 @@ def test_p6_leapfrog_closed_form_constant_hamiltonian():
         assert np.linalg.norm(Dn - r["D"][ik]) / np.linalg.norm(Dn) < 1e-11
 
 
+def test_p6b_frozen_shift_is_the_closed_form_of_its_constant_hamiltonian():
+    """P-6 with the SCC shift frozen (eps_fixed): with gamma != 0 and a kick, H_k
+    = H0 + (eps0_I + eps0_J) S / 2 + (A/c).P + |A|^2/(2c^2) S is constant in time,
+    so the leapfrog from the SCC ground state equals the closed form of P-6 for
+    that H, while the self-consistent run (shift following dq(t)) does not."""
+    s = inputs.diamond_si(1, 0.1, seed=5, kgrid="mp2")
+    ctx = O.setup(s)
+    gs = O.ground_state(s, ctx=ctx)
+    n = 300
+    A = inputs.kick_field(n, 2.0, pol=(1.0, 0.5, -0.2))
+    r = O.propagate(s, A, n, gs["D"], ctx=ctx, eps_fixed=gs["eps"])
+    r_scc = O.propagate(s, A, n, gs["D"], ctx=ctx)
+    dt = s["dt"]
+    eps_orb = gs["eps"][ctx["atom_of"]]
+    assert np.abs(gs["eps"]).max() > 1e-3
+    for ik in (0, 3):
+        H = O.hamiltonian(ctx["H0"][ik], ctx["S"][ik], ctx["P"][ik], A[0], eps_orb)
+        lam, V = sla.eig(ctx["Sinv"][ik] @ H)
+        lam = lam.real
+        Vi = np.linalg.inv(V)
+        X0 = Vi @ gs["D"][ik] @ Vi.conj().T
+        w = lam[:, None] - lam[None, :]
+        rp = -1j * w * dt + np.sqrt(1 - (w * dt) ** 2)
+        rm = -1j * w * dt - np.sqrt(1 - (w * dt) ** 2)
+        x1 = (1 - 1j * w * dt) * X0
+        a = (x1 - rm * X0) / (rp - rm)
+        Dn = V @ (a * rp ** n + (X0 - a) * rm ** n) @ V.conj().T
+        assert np.linalg.norm(Dn - r["D"][ik]) / np.linalg.norm(Dn) < 1e-11
+        assert np.linalg.norm(Dn - r_scc["D"][ik]) / np.linalg.norm(Dn) > 1e-6
+
+
 def test_p7_band_folding_supercell_equals_kgrid(si8):
     """P-7: 64-atom Gamma supercell == 8-atom cell on the Gamma-centred 2x2x2 grid."""
     s8 = inputs.diamond_si(1, 0.0, seed=8, kgrid="gc2")
