@@ -114,7 +114,25 @@ typedef struct {
                                two iterates differ by more than cn_tol in any entry (0 = 1e-10) */
   int tile_variant[2];      /* split form: tile variant of product 1 / product 2 (see
                                vgtb_tile_config; -1 = variant 0, or the autotuner's choice) */
+  int product1;             /* form of the first product W = D H of Eq. 6 (VGTB_P1_*):
+                               AUTO (0, default): the FP64 path runs it block-sparse, the split
+                               form as the dense tcgen05 GEMM (the faster form at 512 atoms);
+                               DENSE: a dense GEMM over all of H_k (8 N^3 flops; FP64 DFMA or
+                               tcgen05 BF16x3); BLOCKS: block-sparse over the nonzero atom blocks
+                               of H_k on the CUDA cores (8 nnz(H) N flops; FP64, or FP32 in the
+                               split form), which needs every atom to carry 4 orbitals (AUTO
+                               falls back to DENSE otherwise, BLOCKS fails with E_UNSUPPORTED) */
+  int scc;                  /* VGTB_SCC_ON (0, default): the shift eps = gamma dq of Eq. 10 follows
+                               the charges at every step; VGTB_SCC_FROZEN: H keeps the shift of
+                               D_k(0) at every step (non-self-consistent propagation); charges,
+                               current and energy are still evaluated from D_k(t_n) */
 } vgtb_options;
+
+#define VGTB_P1_AUTO     0
+#define VGTB_P1_DENSE    1
+#define VGTB_P1_BLOCKS   2
+#define VGTB_SCC_ON      0
+#define VGTB_SCC_FROZEN  1
 
 /* Fill *opt with the defaults above (precision FP64, ground-state init, leapfrog). */
 void vgtb_default_options(vgtb_options* opt);
@@ -231,7 +249,9 @@ int vgtb_kernel_stats(vgtb_ctx* ctx, long long* launches, double* ms, int n);
  * (product 1 = [dD|D0][H|dH]^dagger, product 2 = S^-1 W^dagger), chosen at
  * create (variant 0, or the autotuner's fastest).  cfg[4] = {tile width,
  * pipeline stages, schedule (0 classic, 1 stream-K, 2 whole waves classic and
- * stream-K over the rest), 1 if the tile spans a 2-SM CTA pair}.
+ * stream-K over the rest), 1 if the tile spans a 2-SM CTA pair}.  When the first
+ * product runs block-sparse (VGTB_P1_BLOCKS), product 1 reports {atoms per group,
+ * output rows per CTA, 3, 0}.
  * Errors: E_INVALID (product not 1 or 2, NULL), E_STATE (FP64 context). */
 int vgtb_tile_config(const vgtb_ctx* ctx, int product, int* cfg);
 
@@ -255,14 +275,17 @@ void vgtb_destroy(vgtb_ctx* ctx);
  * The call allocates nothing: its scratch (BF16 pieces, the FP32 product, a
  * problem table and an error word, 2 MiB + 512 B) is one static device array
  * that every GPU which loads the library holds until the process exits.  The
- * first call on a device looks up the array's device address and raises the
- * kernel's shared-memory limit; make that first call before any stream
- * capture.  All calls share the array and it keeps the last call's contents
+ * first call on a device (and the first call after that device's context was
+ * replaced, e.g. by cudaDeviceReset) looks up the array's device address and
+ * raises the kernel's shared-memory limit; make that first call before any
+ * stream capture.  First calls from several host threads are serialised by a
+ * lock inside the library.  All calls share the array and it keeps the last call's contents
  * (each call rewrites, zero padding included, everything it reads), so calls
  * whose work overlaps on the GPU (other streams or host threads) race.
  * Returns VGTB_OK; VGTB_E_INVALID for n outside 1..256 or a NULL pointer;
  * VGTB_E_UNSUPPORTED without an sm_103a device; VGTB_E_TIMEOUT when a bounded
- * device wait expired; VGTB_E_CUDA for a failed CUDA call. */
+ * device wait expired (c is then left unwritten); VGTB_E_CUDA for a failed
+ * CUDA call (the contents of c are then unspecified). */
 int vgtb_split_cgemm_noalloc(int n, const double* a, const double* r, double* c, void* stream);
 
 #ifdef __cplusplus

@@ -28,6 +28,27 @@ int vgtb_diag_split_chain_variant(int n, const double* a, const double* r, const
                                   double* w_out, double* x_out);
 int vgtb_diag_num_variants(void);
 
+/* The library's integer-bit float <-> double conversions (used by the
+ * split-precision kernels on their hot path) run on the device beside the CUDA
+ * conversions, for unit tests.  The paper has no counterpart.
+ * d_in [n] doubles -> f_bits[n] (d2f_bits) and f_ref[n] (__double2float_rn);
+ * f_in [n] floats  -> d_bits[n] (f2d_bits) and d_ref[n] (the exact widening).
+ * All host pointers, caller-owned; n >= 0.  Returns VGTB_OK, VGTB_E_INVALID
+ * (negative n or a NULL pointer with n > 0) or VGTB_E_CUDA.  Allocates and
+ * frees its own device memory. */
+int vgtb_diag_convert(int n, const double* d_in, const float* f_in, float* f_bits, float* f_ref, double* d_bits,
+                      double* d_ref);
+
+/* The bounded device waits of the tcgen05 product kernels, made to run out: one
+ * thread waits, with the kernels' own wait routine, for an mbarrier phase that no
+ * thread completes (which = 0) or for a stream-K partial flag that no CTA sets
+ * (which = 1), limited to limit_ns (1 .. 10^10 ns).  The wait gives up, records
+ * the expiry in an error word and the kernel returns; the call then returns
+ * VGTB_E_TIMEOUT.  VGTB_OK would mean the wait ended without its event (a
+ * defect).  The paper has no counterpart.  Errors: VGTB_E_INVALID (which or
+ * limit out of range), VGTB_E_UNSUPPORTED (no sm_103a device), VGTB_E_CUDA. */
+int vgtb_diag_bounded_wait(long long limit_ns, int which);
+
 #ifdef __cplusplus
 }
 #endif

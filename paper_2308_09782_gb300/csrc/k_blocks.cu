@@ -239,25 +239,17 @@ __device__ __forceinline__ float half_sum_f(float v) {
 // ---------------------------------------------------------------------------
 // k_obs_atoms_split: the split form's observables and per-atom sums in one
 // launch.  One CTA per (trajectory, atom I); its threads take the nonzeros of
-// the atom's rows (all targets (I, J)) and form the dD sums in FP32 (dD
-// converted from the FP64 master with integer operations, k-space blocks as
-// packed FP32 records); warp 0 adds the 8 warp sums in FP64, then the
-// constant D0 part (obs0a) and the A terms (both linear in the sums) and writes
-// dq_I, q_I and the atom's shares of T and of the band energy, as k_scc_atoms
-// does for the FP64 paths.  GB300 issues an FP64 warp instruction at a small
-// fraction of the FP32 rate, whatever the number of active lanes, so FP64 stays
-// in warp 0.  The FP32 rounding of the dD part is far below the BF16x3
-// products' own error.
+// the atom's rows (all targets (I, J)) and form the dD sums in FP64 from the
+// FP64 master dD and the FP64 k-space blocks (S_k, P_k, H0_k), so charges,
+// current and energy keep the precision of the master copy; the 8 warp sums,
+// the constant D0 part (obs0a) and the A terms (both linear in the sums) are
+// added in FP64 too.  Warp 0 writes dq_I, q_I and the atom's shares of T and of
+// the band energy, as k_scc_atoms does for the FP64 paths.  The k loop is
+// outside the element loop so that each k's sums take its weight once.
 // ---------------------------------------------------------------------------
-// 256 threads: two passes over the ~464 nonzeros of an sp3 atom's row block, and
-// every CTA of a 512-atom step resident in one wave (512 threads took 1.1 waves)
+// 256 threads: two passes over the ~490 nonzeros of an sp3 atom's row block, and
+// every CTA of a 512-atom step resident in one wave
 constexpr int kObsAtomThreads = 256;
-
-__device__ __forceinline__ float warp_sum_f(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
 
 __global__ void __launch_bounds__(kObsAtomThreads) k_obs_atoms_split(const DevSys* __restrict__ sysv, DevTraj* trj,
                                                                    const DevItem* __restrict__ items, int n_traj,
@@ -266,7 +258,7 @@ __global__ void __launch_bounds__(kObsAtomThreads) k_obs_atoms_split(const DevSy
   pdl_wait();
   pdl_trigger();
   constexpr int NW = kObsAtomThreads / 32;
-  __shared__ float red[5][NW];
+  __shared__ double red[5][NW];
   const int t = blockIdx.x / max_nat, I = blockIdx.x % max_nat;
   if (t >= n_traj) return;
   DevTraj& T = trj[t];
@@ -275,30 +267,37 @@ __global__ void __launch_bounds__(kObsAtomThreads) k_obs_atoms_split(const DevSy
   const int n = fixed_step >= 0 ? fixed_step : *step;
   const int par = n & 1;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float sS = 0.f, sx = 0.f, sy = 0.f, sz = 0.f, sH = 0.f;
+  double sS = 0.0, sx = 0.0, sy = 0.0, sz = 0.0, sH = 0.0;
   // the atom's nonzeros are contiguous (targets sorted by row atom); el_off gives
   // each one's offset in the Np x Np matrix, so a thread needs no index lookups
   const int e0 = S.el_atom0[I], e1 = S.el_atom0[I + 1];
-  for (int e = e0 + threadIdx.x; e < e1; e += kObsAtomThreads) {
-    const long long off = S.el_off[e];
-    for (int k = 0; k < S.nk; ++k) {
-      const double2 dd = items[T.item0 + k].D[par][off];
-      const float4* kb = S.kf + 3 * ((long long)k * S.n_el + e);
-      const float4 c0 = kb[0], c1 = kb[1], c2 = kb[2];
-      const float dr = d2f_bits(dd.x), di = d2f_bits(dd.y);
-      const float wk = S.wkf[k];
-      sS = fmaf(wk, fmaf(dr, c0.x, di * c0.y), sS);
-      sx = fmaf(wk, fmaf(dr, c0.z, di * c0.w), sx);
-      sy = fmaf(wk, fmaf(dr, c1.x, di * c1.y), sy);
-      sz = fmaf(wk, fmaf(dr, c1.z, di * c1.w), sz);
-      sH = fmaf(wk, fmaf(dr, c2.x, di * c2.y), sH);
+  const long long ps = (long long)S.nk * S.n_el;
+  for (int k = 0; k < S.nk; ++k) {
+    const double2* Dk = items[T.item0 + k].D[par];
+    double cS = 0.0, cx = 0.0, cy = 0.0, cz = 0.0, cH = 0.0;
+    for (int e = e0 + threadIdx.x; e < e1; e += kObsAtomThreads) {
+      const double2 dd = Dk[S.el_off[e]];
+      const long long ke = (long long)k * S.n_el + e;
+      const double2 bs = S.kS[ke], bx = S.kP[ke], by = S.kP[ps + ke], bz = S.kP[2 * ps + ke], bh = S.kH0[ke];
+      // Re(dD conj(X)) for X = S_k, P_k^x, P_k^y, P_k^z, H0_k
+      cS = fma(dd.x, bs.x, fma(dd.y, bs.y, cS));
+      cx = fma(dd.x, bx.x, fma(dd.y, bx.y, cx));
+      cy = fma(dd.x, by.x, fma(dd.y, by.y, cy));
+      cz = fma(dd.x, bz.x, fma(dd.y, bz.y, cz));
+      cH = fma(dd.x, bh.x, fma(dd.y, bh.y, cH));
     }
+    const double w = S.wk[k];
+    sS = fma(w, cS, sS);
+    sx = fma(w, cx, sx);
+    sy = fma(w, cy, sy);
+    sz = fma(w, cz, sz);
+    sH = fma(w, cH, sH);
   }
-  sS = warp_sum_f(sS);
-  sx = warp_sum_f(sx);
-  sy = warp_sum_f(sy);
-  sz = warp_sum_f(sz);
-  sH = warp_sum_f(sH);
+  sS = warp_sum(sS);
+  sx = warp_sum(sx);
+  sy = warp_sum(sy);
+  sz = warp_sum(sz);
+  sH = warp_sum(sH);
   if (lane == 0) {
     red[0][warp] = sS;
     red[1][warp] = sx;
@@ -311,7 +310,7 @@ __global__ void __launch_bounds__(kObsAtomThreads) k_obs_atoms_split(const DevSy
   const int l = threadIdx.x;
   double v[5];
 #pragma unroll
-  for (int i = 0; i < 5; ++i) v[i] = warp_sum(l < NW ? f2d_bits(red[i][l]) : 0.0);
+  for (int i = 0; i < 5; ++i) v[i] = warp_sum(l < NW ? red[i][l] : 0.0);
   if (l != 0) return;
   const double* o = S.obs0a + 5LL * I;
 #pragma unroll
@@ -346,22 +345,6 @@ void launch_obs(const DevSys* sys, const DevTraj* trj, const DevItem* items, con
   const int blocks = (total_units * 16 + threads - 1) / threads;
   launch_pdl(k_obs, blocks, threads, 0, st, sys, trj, items, warp_prefix, n_traj, total_units, step, delta,
              fixed_step);
-}
-
-// Setup (split form): packed FP32 copies of the k-space blocks for k_obs_split.
-__global__ void k_kblocks_f32(const DevSys* __restrict__ sysv, int s_idx, long long n) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;  // over nk * n_el
-  const DevSys& S = sysv[s_idx];
-  if (i >= n) return;
-  const long long ps = (long long)S.nk * S.n_el;
-  const double2 s = S.kS[i], px = S.kP[i], py = S.kP[ps + i], pz = S.kP[2 * ps + i], h = S.kH0[i];
-  S.kf[3 * i] = make_float4((float)s.x, (float)s.y, (float)px.x, (float)px.y);
-  S.kf[3 * i + 1] = make_float4((float)py.x, (float)py.y, (float)pz.x, (float)pz.y);
-  S.kf[3 * i + 2] = make_float4((float)h.x, (float)h.y, 0.f, 0.f);
-}
-
-void launch_kblocks_f32(const DevSys* sys, int s_idx, long long n, cudaStream_t st) {
-  k_kblocks_f32<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(sys, s_idx, n);
 }
 
 // ---------------------------------------------------------------------------
@@ -452,11 +435,14 @@ __global__ void __launch_bounds__(kSccThreads) k_scc_eps(const DevSys* __restric
     }
     const double e = warp_sum((e0 + e1) + (e2 + e3));
     if (lane == 0) {
-      T.eps[I] = e;
-      if (T.eps_lv) T.eps_lv[(long long)(n & 1) * S.nat + I] = e;
+      // the Hamiltonian's shift: gamma dq (Eq. 10), or the shift of D(0) when
+      // frozen; the energy below uses gamma dq either way
+      const double eh = S.scc_frozen ? S.eps0[I] : e;
+      T.eps[I] = eh;
+      if (T.eps_lv) T.eps_lv[(long long)(n & 1) * S.nat + I] = eh;
       if (T.epsf) {
-        T.epsf[I] = (float)e;
-        T.depsf[I] = (float)(e - S.eps0[I]);
+        T.epsf[I] = (float)eh;
+        T.depsf[I] = (float)(eh - S.eps0[I]);
       }
       // this atom's shares of T_x, T_y, T_z, the band energy, dq.eps and the electron count
       const double* a = T.apart + 4LL * I;
@@ -595,8 +581,15 @@ __global__ void __launch_bounds__(256) k_phase(const DevSys* __restrict__ sysv, 
         dr += ph.x * wr - ph.y * adS;
         di += ph.x * adS + ph.y * wr;
       }
-      it.H[idx] = make_double2(hr, hi);
-      if (mode == PH_FP64_DELTA) it.dH[idx] = make_double2(dr, di);
+      if (it.kH) {
+        // block-sparse first product: the target's elements, in target order
+        const long long ce = S.tgt_el0[U.tg] + e;
+        reinterpret_cast<double2*>(it.kH)[ce] = make_double2(hr, hi);
+        if (mode == PH_FP64_DELTA) reinterpret_cast<double2*>(it.kdH)[ce] = make_double2(dr, di);
+      } else {
+        it.H[idx] = make_double2(hr, hi);
+        if (mode == PH_FP64_DELTA) it.dH[idx] = make_double2(dr, di);
+      }
     }
   }
 }
@@ -611,8 +604,9 @@ void launch_phase(const DevSys* sys, const DevTraj* trj, const DevItem* items, c
 
 // ---------------------------------------------------------------------------
 // Phase build, split form: the delta-form H and dH summed in FP32 and stored
-// as the embedded real matrix [[Re, Im], [-Im, Re]] in BF16 hi/lo pieces, the
-// B operand of the first product.
+// either at the target elements in FP32 (block-sparse first product) or as the
+// embedded real matrix [[Re, Im], [-Im, Re]] in BF16 hi/lo pieces (the B
+// operand of the dense tcgen05 first product).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void store_emb_f(__nv_bfloat16* base, int Np, int r, int c, float re, float im) {
   const long long P = 4LL * Np * Np;
@@ -736,8 +730,20 @@ __global__ void __launch_bounds__(256, 4) k_phase_split(const DevSys* __restrict
             di[j] += ph.x * adS + ph.y * wr;
           }
         }
-        store_emb_f4(it.Hemb_p, S.Np, oi + r, oj, hr, hi);
-        store_emb_f4(it.dHemb_p, S.Np, oi + r, oj, dr, di);
+        if (it.kH) {
+          // block-sparse first product: row r of the target's 4 x 4 block (every
+          // atom has 4 orbitals there, so the element index is a multiple of 4)
+          const long long ce = S.tgt_el0[U.tg] + 4LL * r;
+          float4* h4 = reinterpret_cast<float4*>(reinterpret_cast<float2*>(it.kH) + ce);
+          float4* d4 = reinterpret_cast<float4*>(reinterpret_cast<float2*>(it.kdH) + ce);
+          h4[0] = make_float4(hr[0], hi[0], hr[1], hi[1]);
+          h4[1] = make_float4(hr[2], hi[2], hr[3], hi[3]);
+          d4[0] = make_float4(dr[0], di[0], dr[1], di[1]);
+          d4[1] = make_float4(dr[2], di[2], dr[3], di[3]);
+        } else {
+          store_emb_f4(it.Hemb_p, S.Np, oi + r, oj, hr, hi);
+          store_emb_f4(it.dHemb_p, S.Np, oi + r, oj, dr, di);
+        }
       }
     } else {
       for (int e = sub; e < nel; e += 4) {
@@ -755,8 +761,14 @@ __global__ void __launch_bounds__(256, 4) k_phase_split(const DevSys* __restrict
           dr += ph.x * wr - ph.y * adS;
           di += ph.x * adS + ph.y * wr;
         }
-        store_emb_f(it.Hemb_p, S.Np, oi + a, oj + b, hr, hi);
-        store_emb_f(it.dHemb_p, S.Np, oi + a, oj + b, dr, di);
+        if (it.kH) {
+          const long long ce = S.tgt_el0[U.tg] + e;
+          reinterpret_cast<float2*>(it.kH)[ce] = make_float2(hr, hi);
+          reinterpret_cast<float2*>(it.kdH)[ce] = make_float2(dr, di);
+        } else {
+          store_emb_f(it.Hemb_p, S.Np, oi + a, oj + b, hr, hi);
+          store_emb_f(it.dHemb_p, S.Np, oi + a, oj + b, dr, di);
+        }
       }
     }
   }

@@ -232,9 +232,10 @@ void launch_leap(const LeapItem* items, int n_items, int Np_max, int x_f32, cons
 // Leapfrog of the split form: X (FP32 planar) and R0 (FP32 planar) give
 // dD/dt in FP32 with the same mirror-exact operations as k_leap; only the
 // master update dD_{n+1} = dD_{n-1} + 2 dt dD/dt is FP64 (GB300's FP64 rate is
-// low, so FP64 is kept to the accumulation that needs it).  The BF16 hi/lo
-// pieces of the new level (A operand of the next first product) are split
-// from its FP32 rounding.
+// low, so FP64 is kept to the accumulation that needs it).  The operand of the
+// next first product is written from the new level's FP32 rounding: its FP32
+// copy (block-sparse product) and/or its BF16 hi/lo pieces (dense tcgen05
+// product).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256, 5) k_leap_split(const LeapItem* __restrict__ items, const int* step, double dt,
                                                     int* counter, int* step_rw) {
@@ -301,11 +302,14 @@ __global__ void __launch_bounds__(256, 5) k_leap_split(const LeapItem* __restric
         const double2 v = make_double2(fma(coef, f2d_bits(dr), b[j].x), fma(coef, f2d_bits(di), b[j].y));
         it.D[nxt][idx] = v;
         const float fr = d2f_bits(v.x), fi = d2f_bits(v.y);
-        const __nv_bfloat16 rh = __float2bfloat16_rn(fr), ih = __float2bfloat16_rn(fi);
-        it.pieces[pr] = rh;
-        it.pieces[P + pr] = __float2bfloat16_rn(fr - __bfloat162float(rh));
-        it.pieces[pr + Np] = ih;
-        it.pieces[P + pr + Np] = __float2bfloat16_rn(fi - __bfloat162float(ih));
+        if (it.f32) it.f32[idx] = make_float2(fr, fi);
+        if (it.pieces) {
+          const __nv_bfloat16 rh = __float2bfloat16_rn(fr), ih = __float2bfloat16_rn(fi);
+          it.pieces[pr] = rh;
+          it.pieces[P + pr] = __float2bfloat16_rn(fr - __bfloat162float(rh));
+          it.pieces[pr + Np] = ih;
+          it.pieces[P + pr + Np] = __float2bfloat16_rn(fi - __bfloat162float(ih));
+        }
       }
     }
   }
@@ -345,6 +349,19 @@ __global__ void k_to_planar_f32(const double2* src, float* dst, int Np) {
 void launch_to_planar_f32(const double2* src, float* dst, int Np, cudaStream_t st) {
   const long long tot = (long long)Np * Np;
   k_to_planar_f32<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(src, dst, Np);
+}
+
+// complex128 -> complex64 with the leapfrog's own rounding (d2f_bits), so a
+// copy rebuilt from a restored level equals the one the leapfrog wrote
+__global__ void k_to_f32(const double2* src, float2* dst, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double2 v = src[i];
+  dst[i] = make_float2(d2f_bits(v.x), d2f_bits(v.y));
+}
+
+void launch_to_f32(const double2* src, float2* dst, long long n, cudaStream_t st) {
+  k_to_f32<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(src, dst, n);
 }
 
 // ---------------------------------------------------------------------------

@@ -284,12 +284,13 @@ int tc_build_plans(const std::vector<TcSysView>& sys, const std::vector<DevItem>
     *msg = "tile variant index out of range";
     return -1;
   }
-  *p1 = *p2 = nullptr;
+  if (p1) *p1 = nullptr;
+  *p2 = nullptr;
   if (configure_all() != cudaSuccess) {
     *msg = "cannot raise the shared-memory limit of the tcgen05 kernels";
     return -1;
   }
-  for (int epi = 0; epi < 2; ++epi) {
+  for (int epi = p1 ? 0 : 1; epi < 2; ++epi) {
     TcPlan* best = nullptr;
     double best_ms = 1e30;
     // the pair kernel handles every Np (a multiple of 128), so variant 0 always applies

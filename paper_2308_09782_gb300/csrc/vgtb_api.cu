@@ -55,6 +55,9 @@ struct HostSys {
   bool density_set = false;
   std::vector<int> trajs;  // trajectories of this system
   std::vector<char> k_set;  // which k-points received a user density
+  float2* D0f = nullptr;    // split form, block-sparse first product: [nk][Np][Np] FP32 copy of D0
+  int bsr_units = 0;        // block-sparse first product: CTAs per item (groups x column chunks)
+  int bsr_tg_max = 0;       // most targets of one atom group
 };
 
 struct HostTraj {
@@ -112,6 +115,11 @@ struct vgtb_ctx {
   // tcgen05 plans
   TcPlan* tc1 = nullptr;
   TcPlan* tc2 = nullptr;
+  // block-sparse first product (every atom 4 orbitals; product1 BLOCKS, or AUTO on the FP64 path)
+  bool bsr = false;
+  BsrItem* d_bsr = nullptr;
+  BsrSys* d_bsrsys = nullptr;
+  int bsr_units_max = 0, bsr_tg_max = 0;
   // graph
   cudaGraphExec_t graph = nullptr;
   int graph_steps = 0;
@@ -322,6 +330,7 @@ int prepare_system(vgtb_ctx* ctx, int si, const vgtb_system& s, HostSys& h, DevS
   memset(&d, 0, sizeof(d));
   d.N = h.N;
   d.Np = h.Np;
+  d.scc_frozen = ctx->opt.scc == VGTB_SCC_FROZEN ? 1 : 0;
   d.nat = h.nat;
   d.nk = h.nk;
   d.n_tgt = h.n_tgt;
@@ -422,13 +431,6 @@ int prepare_system(vgtb_ctx* ctx, int si, const vgtb_system& s, HostSys& h, DevS
   TRY(dalloc(ctx, &d.kS, (size_t)h.nk * h.n_el));
   TRY(dalloc(ctx, &d.kH0, (size_t)h.nk * h.n_el));
   TRY(dalloc(ctx, &d.kP, 3 * (size_t)h.nk * h.n_el));
-  if (ctx->split) {
-    TRY(dalloc(ctx, &d.kf, 3 * (size_t)h.nk * h.n_el));
-    std::vector<float> wf(h.wk.begin(), h.wk.end());
-    float* pwf;
-    TRY(upload(ctx, &pwf, wf.data(), wf.size()));
-    d.wkf = pwf;
-  }
   TRY(dalloc(ctx, &d.obs0, 5 * (size_t)h.n_tgt));
   if (ctx->split) TRY(dalloc(ctx, &d.obs0a, 5 * (size_t)h.nat));
   const size_t NN = (size_t)h.Np * h.Np;
@@ -463,7 +465,6 @@ int build_sinv(vgtb_ctx* ctx, int si) {
   HostSys& h = ctx->sys[si];
   const size_t NN = (size_t)h.Np * h.Np;
   for (int k = 0; k < h.nk; ++k) launch_kblocks(ctx->d_sys, si, h.n_tgt, k, ctx->stream);
-  if (ctx->split) launch_kblocks_f32(ctx->d_sys, si, (long long)h.nk * h.n_el, ctx->stream);
   int* info = nullptr;
   TRY(dalloc(ctx, &info, 1));
   for (int k = 0; k < h.nk; ++k) {
@@ -501,6 +502,63 @@ int build_sinv(vgtb_ctx* ctx, int si) {
 }
 
 // charges of a density set D (nk x Np^2) of system si: q_I on the host
+// ---------------------------------------------------------------------------
+// Block-sparse first product: groups of G consecutive atoms; for each group the
+// union of the column atoms K of its targets (J, K), and for every member J the
+// index of target (J, K) relative to the group's first target (-1 if none).
+// The group's targets are contiguous because targets are sorted by row atom.
+// ---------------------------------------------------------------------------
+bool bsr_possible(const HostSys& h) {
+  for (int i = 0; i < h.nat; ++i)
+    if (h.orb_off[i + 1] - h.orb_off[i] != 4) return false;
+  return true;
+}
+
+int build_bsr_tables(vgtb_ctx* ctx, HostSys& h, int fp64, BsrSys& b) {
+  const int G = bsr_group(fp64);
+  const int n_grp = (h.nat + G - 1) / G;
+  std::vector<int> grp_t0(n_grp + 1), grp_e0(n_grp + 1, 0), ent_K;
+  std::vector<short> ent_slot;
+  int tg_max = 0;
+  for (int g = 0; g < n_grp; ++g) {
+    const int J0 = g * G, J1 = std::min(h.nat, J0 + G);
+    const int t0 = h.atom_tgt0[J0], t1 = h.atom_tgt0[J1];
+    grp_t0[g] = t0;
+    tg_max = std::max(tg_max, t1 - t0);
+    if (t1 - t0 > 32767) return fail(ctx, VGTB_E_UNSUPPORTED, "atom group with %d targets", t1 - t0);
+    std::map<int, std::vector<short>> uni;  // column atom -> slots of the members
+    for (int J = J0; J < J1; ++J)
+      for (int t = h.atom_tgt0[J]; t < h.atom_tgt0[J + 1]; ++t) {
+        auto& v = uni[h.tgt_J[t]];
+        if (v.empty()) v.assign(G, (short)-1);
+        v[J - J0] = (short)(t - t0);
+      }
+    for (auto& kv : uni) {
+      ent_K.push_back(kv.first);
+      ent_slot.insert(ent_slot.end(), kv.second.begin(), kv.second.end());
+    }
+    grp_e0[g + 1] = (int)ent_K.size();
+  }
+  grp_t0[n_grp] = h.atom_tgt0[h.nat];
+  memset(&b, 0, sizeof(b));
+  b.Np = h.Np;
+  b.nat = h.nat;
+  b.n_grp = n_grp;
+  int* pi;
+  TRY(upload(ctx, &pi, grp_t0.data(), grp_t0.size()));
+  b.grp_t0 = pi;
+  TRY(upload(ctx, &pi, grp_e0.data(), grp_e0.size()));
+  b.grp_e0 = pi;
+  TRY(upload(ctx, &pi, ent_K.data(), ent_K.size()));
+  b.ent_K = pi;
+  short* ps;
+  TRY(upload(ctx, &ps, ent_slot.data(), ent_slot.size()));
+  b.ent_slot = ps;
+  h.bsr_units = bsr_units(fp64, n_grp, h.Np);
+  h.bsr_tg_max = tg_max;
+  return VGTB_OK;
+}
+
 int host_charges(vgtb_ctx* ctx, int si, const double2* D, std::vector<double>& q) {
   HostSys& h = ctx->sys[si];
   double* part = nullptr;
@@ -723,7 +781,8 @@ int finish_density(vgtb_ctx* ctx, int si) {
   }
   if (ctx->split) {
     for (int k = 0; k < h.nk; ++k) {
-      launch_split_planar(h.D0 + k * NN, h.D0_p + 4 * NN * k, h.N, h.Np, ctx->stream);
+      if (h.D0f) launch_to_f32(h.D0 + k * NN, h.D0f + k * NN, (long long)NN, ctx->stream);
+      if (h.D0_p) launch_split_planar(h.D0 + k * NN, h.D0_p + 4 * NN * k, h.N, h.Np, ctx->stream);
       launch_split_planar(h.Sinv + k * NN, h.Sinv_p + 4 * NN * k, h.N, h.Np, ctx->stream);
       launch_to_planar_f32(h.R0 + k * NN, h.R0f + 2 * NN * k, h.Np, ctx->stream);
     }
@@ -747,6 +806,7 @@ int reset_all(vgtb_ctx* ctx) {
       CK(cudaMemcpyAsync(it.Cd, h.C0d + (size_t)it.k * h.nocc * h.Np, (size_t)h.nocc * h.Np * sizeof(double2),
                          cudaMemcpyDeviceToDevice, ctx->stream));
     if (it.dD_p) CK(cudaMemsetAsync(it.dD_p, 0, 4 * NN * sizeof(__nv_bfloat16), ctx->stream));
+    if (it.dDf) CK(cudaMemsetAsync(it.dDf, 0, NN * sizeof(float2), ctx->stream));
   }
   for (auto& t : ctx->trj) CK(cudaMemsetAsync(t.status, 0, sizeof(int), ctx->stream));
   CK(cudaMemsetAsync(ctx->d_step, 0, sizeof(int), ctx->stream));
@@ -929,12 +989,16 @@ int enqueue_step(vgtb_ctx* ctx, cudaEvent_t* ev) {
     launch_phase(ctx->d_sys, ctx->d_trj, ctx->d_items, ctx->d_wpre, nt, ctx->total_warps, ctx->d_step,
                  ctx->delta ? PH_FP64_DELTA : PH_FP64_PLAIN, -1, st);
   if (ev) CK(cudaEventRecordWithFlags(ev[3], st, evflag));
+  if (ctx->bsr)
+    launch_bsr(ctx->d_bsr, ctx->d_bsrsys, ctx->n_items, ctx->bsr_units_max, ctx->split ? 0 : 1, ctx->bsr_tg_max,
+               ctx->d_step, st);
   if (ctx->split) {
-    TRY(tc_launch(ctx->tc1, st) == 0 ? VGTB_OK : fail(ctx, VGTB_E_CUDA, "tcgen05 product 1 launch failed"));
+    if (!ctx->bsr)
+      TRY(tc_launch(ctx->tc1, st) == 0 ? VGTB_OK : fail(ctx, VGTB_E_CUDA, "tcgen05 product 1 launch failed"));
     if (ev) CK(cudaEventRecordWithFlags(ev[4], st, evflag));
     TRY(tc_launch(ctx->tc2, st) == 0 ? VGTB_OK : fail(ctx, VGTB_E_CUDA, "tcgen05 product 2 launch failed"));
   } else {
-    launch_gemm_f64(ctx->d_g1, ctx->n_items, ctx->max_Np, ctx->max_Np, ctx->d_step, st);
+    if (!ctx->bsr) launch_gemm_f64(ctx->d_g1, ctx->n_items, ctx->max_Np, ctx->max_Np, ctx->d_step, st);
     if (ev) CK(cudaEventRecordWithFlags(ev[4], st, evflag));
     launch_gemm_f64(ctx->d_g2, ctx->n_items, ctx->max_Np, ctx->max_Np, ctx->d_step, st);
   }
@@ -1063,6 +1127,10 @@ int vgtb_create_batch(vgtb_ctx** out, int n_sys, const vgtb_system* sys, int n_t
     return bail(fail(ctx, VGTB_E_INVALID, "unknown init %d", ctx->opt.init));
   if (ctx->opt.integrator != VGTB_LEAPFROG && ctx->opt.integrator != VGTB_CRANK_NICOLSON)
     return bail(fail(ctx, VGTB_E_INVALID, "unknown integrator %d", ctx->opt.integrator));
+  if (ctx->opt.scc != VGTB_SCC_ON && ctx->opt.scc != VGTB_SCC_FROZEN)
+    return bail(fail(ctx, VGTB_E_INVALID, "unknown scc mode %d", ctx->opt.scc));
+  if (ctx->opt.product1 < VGTB_P1_AUTO || ctx->opt.product1 > VGTB_P1_BLOCKS)
+    return bail(fail(ctx, VGTB_E_INVALID, "unknown product1 form %d", ctx->opt.product1));
   ctx->split = ctx->opt.precision == VGTB_SPLIT_BF16X3;
   ctx->cn = ctx->opt.integrator == VGTB_CRANK_NICOLSON;
   if (ctx->cn && ctx->split)
@@ -1106,6 +1174,34 @@ int vgtb_create_batch(vgtb_ctx** out, int n_sys, const vgtb_system* sys, int n_t
     ctx->max_Np = std::max(ctx->max_Np, ctx->sys[s].Np);
   }
   if (scc_configure(ctx->max_nat)) return bail(fail(ctx, VGTB_E_CUDA, "k_scc shared memory configuration failed"));
+  // block-sparse first product when every atom of every system carries 4 orbitals
+  // block-sparse first product: asked for, or by default on the FP64 path (on
+  // the split form the dense tcgen05 product is faster at these sizes)
+  bool blocks_ok = true;
+  for (auto& h : ctx->sys) blocks_ok = blocks_ok && bsr_possible(h);
+  if (ctx->opt.product1 == VGTB_P1_BLOCKS && (!blocks_ok || ctx->cn))
+    return bail(fail(ctx, VGTB_E_UNSUPPORTED, "block-sparse first product needs 4 orbitals on every atom and the "
+                     "leapfrog integrator"));
+  ctx->bsr = !ctx->cn && blocks_ok &&
+             (ctx->opt.product1 == VGTB_P1_BLOCKS || (ctx->opt.product1 == VGTB_P1_AUTO && !ctx->split));
+  std::vector<BsrSys> bsys(n_sys);
+  if (ctx->bsr) {
+    for (int s = 0; s < n_sys; ++s) {
+      if ((rc = build_bsr_tables(ctx, ctx->sys[s], ctx->split ? 0 : 1, bsys[s]))) return bail(rc);
+      ctx->bsr_units_max = std::max(ctx->bsr_units_max, ctx->sys[s].bsr_units);
+      ctx->bsr_tg_max = std::max(ctx->bsr_tg_max, ctx->sys[s].bsr_tg_max);
+    }
+    if (bsr_configure(ctx->split ? 0 : 1, ctx->bsr_tg_max))
+      return bail(fail(ctx, VGTB_E_UNSUPPORTED, "block-sparse product: %d targets per atom group exceed shared memory",
+                       ctx->bsr_tg_max));
+    if ((rc = upload(ctx, &ctx->d_bsrsys, bsys.data(), bsys.size()))) return bail(rc);
+    if (ctx->split)
+      for (int s = 0; s < n_sys; ++s) {
+        HostSys& h = ctx->sys[s];
+        if ((rc = dalloc(ctx, &h.D0f, (size_t)h.nk * h.Np * h.Np))) return bail(rc);
+        dsys[s].D0f = h.D0f;
+      }
+  }
   if ((rc = upload(ctx, &ctx->d_sys, dsys.data(), dsys.size()))) return bail(rc);
   // trajectories and items; the split form keeps each operand family of a
   // system contiguous over its items so that one 4-D tensor map covers it
@@ -1122,9 +1218,11 @@ int vgtb_create_batch(vgtb_ctx** out, int n_sys, const vgtb_system* sys, int n_t
     for (int s = 0; s < n_sys; ++s) {
       const size_t NN = (size_t)ctx->sys[s].Np * ctx->sys[s].Np, ni = sys_items[s];
       if (ni == 0) continue;
-      if ((rc = dalloc(ctx, &fam[s].dD, 4 * NN * ni))) return bail(rc);
-      if ((rc = dalloc(ctx, &fam[s].Hemb, 8 * NN * ni))) return bail(rc);
-      if ((rc = dalloc(ctx, &fam[s].dHemb, 8 * NN * ni))) return bail(rc);
+      if (!ctx->bsr) {
+        if ((rc = dalloc(ctx, &fam[s].dD, 4 * NN * ni))) return bail(rc);
+        if ((rc = dalloc(ctx, &fam[s].Hemb, 8 * NN * ni))) return bail(rc);
+        if ((rc = dalloc(ctx, &fam[s].dHemb, 8 * NN * ni))) return bail(rc);
+      }
       if ((rc = dalloc(ctx, &fam[s].Wemb, 8 * NN * ni))) return bail(rc);
       if ((rc = dalloc(ctx, &fam[s].Xf, 2 * NN * ni))) return bail(rc);
     }
@@ -1150,9 +1248,18 @@ int vgtb_create_batch(vgtb_ctx** out, int n_sys, const vgtb_system* sys, int n_t
       it.D[1] = ctx->cn ? lv : lv + NN;
       if (ctx->split) {
         const size_t li = sys_next[T.sys]++;
-        it.dD_p = fam[T.sys].dD + 4 * NN * li;
-        it.Hemb_p = fam[T.sys].Hemb + 8 * NN * li;
-        it.dHemb_p = fam[T.sys].dHemb + 8 * NN * li;
+        if (ctx->bsr) {
+          float2 *kh = nullptr, *kdh = nullptr;
+          if ((rc = dalloc(ctx, &it.dDf, NN))) return bail(rc);
+          if ((rc = dalloc(ctx, &kh, (size_t)h.n_el))) return bail(rc);
+          if ((rc = dalloc(ctx, &kdh, (size_t)h.n_el))) return bail(rc);
+          it.kH = kh;
+          it.kdH = kdh;
+        } else {
+          it.dD_p = fam[T.sys].dD + 4 * NN * li;
+          it.Hemb_p = fam[T.sys].Hemb + 8 * NN * li;
+          it.dHemb_p = fam[T.sys].dHemb + 8 * NN * li;
+        }
         it.Wemb_p = fam[T.sys].Wemb + 8 * NN * li;
         it.Xf = fam[T.sys].Xf + 2 * NN * li;
       } else if (ctx->cn) {
@@ -1163,10 +1270,18 @@ int vgtb_create_batch(vgtb_ctx** out, int n_sys, const vgtb_system* sys, int n_t
         if ((rc = dalloc(ctx, &it.Y[0], nc))) return bail(rc);
         if ((rc = dalloc(ctx, &it.Y[1], nc))) return bail(rc);
       } else {
-        if ((rc = dalloc(ctx, &it.H, NN))) return bail(rc);
+        if (ctx->bsr) {
+          double2 *kh = nullptr, *kdh = nullptr;
+          if ((rc = dalloc(ctx, &kh, (size_t)h.n_el))) return bail(rc);
+          if (ctx->delta && (rc = dalloc(ctx, &kdh, (size_t)h.n_el))) return bail(rc);
+          it.kH = kh;
+          it.kdH = kdh;
+        } else {
+          if ((rc = dalloc(ctx, &it.H, NN))) return bail(rc);
+          if (ctx->delta && (rc = dalloc(ctx, &it.dH, NN))) return bail(rc);
+        }
         if ((rc = dalloc(ctx, &it.W, NN))) return bail(rc);
         if ((rc = dalloc(ctx, &it.X, NN))) return bail(rc);
-        if (ctx->delta && (rc = dalloc(ctx, &it.dH, NN))) return bail(rc);
       }
       ctx->items_h.push_back(it);
     }
@@ -1231,6 +1346,7 @@ int vgtb_create_batch(vgtb_ctx** out, int n_sys, const vgtb_system* sys, int n_t
     l.D[0] = it.D[0];
     l.D[1] = it.D[1];
     l.pieces = it.dD_p;
+    l.f32 = it.dDf;
     l.Np = h.Np;
     l.mode = 0;
     lv[i] = l;
@@ -1242,6 +1358,31 @@ int vgtb_create_batch(vgtb_ctx** out, int n_sys, const vgtb_system* sys, int n_t
     if ((rc = upload(ctx, &ctx->d_g2, g2.data(), g2.size()))) return bail(rc);
   }
   if ((rc = upload(ctx, &ctx->d_leap, lv.data(), lv.size()))) return bail(rc);
+  if (ctx->bsr) {
+    std::vector<BsrItem> bl(ctx->n_items);
+    for (int i = 0; i < ctx->n_items; ++i) {
+      const DevItem& it = ctx->items_h[i];
+      const HostSys& h = ctx->sys[it.sys];
+      const size_t NN = (size_t)h.Np * h.Np;
+      BsrItem b{};
+      b.sys = it.sys;
+      b.nseg = ctx->delta ? 2 : 1;
+      b.R[0] = it.kH;
+      b.R[1] = it.kdH;
+      if (ctx->split) {
+        b.A[0] = it.dDf;                       // FP32 copy of the current dD level
+        b.A[1] = h.D0f + it.k * NN;
+        b.W = it.Wemb_p;
+      } else {
+        b.A[0] = it.D[0];                      // level of the step's parity
+        b.a_par = (long long)NN;
+        b.A[1] = ctx->delta ? (const void*)(h.D0 + it.k * NN) : nullptr;
+        b.W = it.W;
+      }
+      bl[i] = b;
+    }
+    if ((rc = upload(ctx, &ctx->d_bsr, bl.data(), bl.size()))) return bail(rc);
+  }
   // setup: S^-1, ground state
   for (int s = 0; s < n_sys; ++s) {
     if ((rc = build_sinv(ctx, s))) return bail(rc);
@@ -1261,7 +1402,7 @@ int vgtb_create_batch(vgtb_ctx** out, int n_sys, const vgtb_system* sys, int n_t
     }
     std::string msg;
     if (tc_build_plans(views, ctx->items_h, ctx->opt.timeout_ns, ctx->opt.autotune, ctx->opt.tile_variant, ctx->stream,
-                       &ctx->tc1, &ctx->tc2, &msg))
+                       ctx->bsr ? nullptr : &ctx->tc1, &ctx->tc2, &msg))
       return bail(fail(ctx, VGTB_E_CUDA, "tcgen05 plan: %s", msg.c_str()));
   }
   if (ctx->opt.init == VGTB_INIT_GROUND) {
@@ -1604,6 +1745,7 @@ int vgtb_set_state(vgtb_ctx* ctx, const void* buf, long long bytes) {
     }
     CK(cudaMemcpyAsync(it.D[0], p, 2 * NN * sizeof(double2), cudaMemcpyHostToDevice, ctx->stream));
     if (it.dD_p) launch_split_planar(it.D[n & 1], it.dD_p, h.N, h.Np, ctx->stream);
+    if (it.dDf) launch_to_f32(it.D[n & 1], it.dDf, (long long)NN, ctx->stream);
     p += 2 * NN * sizeof(double2);
   }
   if (ctx->cn)
@@ -1641,6 +1783,13 @@ int vgtb_kernel_stats(vgtb_ctx* ctx, long long* launches, double* ms, int n) {
 int vgtb_tile_config(const vgtb_ctx* ctx, int product, int* cfg) {
   if (!ctx || !cfg || (product != 1 && product != 2)) return VGTB_E_INVALID;
   if (!ctx->split) return VGTB_E_STATE;
+  if (product == 1 && ctx->bsr) {
+    cfg[0] = bsr_group(0);   // atoms per group (output columns / 4)
+    cfg[1] = kBsrThreads;    // output rows per CTA
+    cfg[2] = 3;              // block-sparse CUDA-core product
+    cfg[3] = 0;
+    return VGTB_OK;
+  }
   return tc_variant_info(tc_plan_variant(product == 1 ? ctx->tc1 : ctx->tc2), cfg) == 0 ? VGTB_OK : VGTB_E_STATE;
 }
 

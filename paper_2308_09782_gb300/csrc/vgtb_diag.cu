@@ -1,11 +1,14 @@
 // vgtb_diag_split_chain: the two tcgen05 products on caller matrices (unit test hook).
 #include <cuda_runtime.h>
 
+#include <cstring>
+
 #include <string>
 #include <vector>
 
 #include "../../include/vgtb.h"
 #include "../../include/vgtb_diag.h"
+#include "tc_kernel.cuh"
 #include "vgtb_internal.h"
 #include "vgtb_tc.h"
 
@@ -111,4 +114,83 @@ extern "C" int vgtb_diag_split_chain_variant(int n, const double* a, const doubl
       x_out[o + 1] = xh[i * ld + Np + j];
     }
   return VGTB_OK;
+}
+
+namespace {
+__global__ void k_diag_convert(int n, const double* d_in, const float* f_in, float* fb, float* fr, double* db,
+                               double* dr) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  fb[i] = d2f_bits(d_in[i]);
+  fr[i] = __double2float_rn(d_in[i]);
+  db[i] = f2d_bits(f_in[i]);
+  dr[i] = (double)f_in[i];
+}
+}  // namespace
+
+extern "C" int vgtb_diag_convert(int n, const double* d_in, const float* f_in, float* f_bits, float* f_ref,
+                                 double* d_bits, double* d_ref) {
+  if (n < 0) return VGTB_E_INVALID;
+  if (n == 0) return VGTB_OK;
+  if (!d_in || !f_in || !f_bits || !f_ref || !d_bits || !d_ref) return VGTB_E_INVALID;
+  Scratch sc;
+  double* di = sc.get<double>(n);
+  float* fi = sc.get<float>(n);
+  float* fb = sc.get<float>(n);
+  float* fr = sc.get<float>(n);
+  double* db = sc.get<double>(n);
+  double* dr = sc.get<double>(n);
+  if (!di || !fi || !fb || !fr || !db || !dr) return VGTB_E_CUDA;
+  if (cudaMemcpy(di, d_in, sizeof(double) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(fi, f_in, sizeof(float) * n, cudaMemcpyHostToDevice) != cudaSuccess)
+    return VGTB_E_CUDA;
+  k_diag_convert<<<(n + 255) / 256, 256>>>(n, di, fi, fb, fr, db, dr);
+  if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) return VGTB_E_CUDA;
+  if (cudaMemcpy(f_bits, fb, sizeof(float) * n, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(f_ref, fr, sizeof(float) * n, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(d_bits, db, sizeof(double) * n, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(d_ref, dr, sizeof(double) * n, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return VGTB_E_CUDA;
+  return VGTB_OK;
+}
+
+namespace {
+// One thread waits for an event that never happens, with the product kernels'
+// bounded wait routines: mbar_wait on a phase nobody completes, or sk_wait_flag
+// on a flag nobody sets.  Both give up after P.timeout_ns and set a bit of *P.err.
+__global__ void k_diag_wait(const __grid_constant__ TcParams P, int which) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x != 0) return;
+  abort_flag = 0;
+  const uint32_t b = smem_u32(&bar);
+  mbar_init(b, 1);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  bool ok;
+  if (which == 0)
+    ok = mbar_wait(b, 0, P.timeout_ns, &abort_flag, P.err);
+  else
+    ok = sk_wait_flag(P, 0, &abort_flag);
+  if (ok) atomicOr(P.err, 16);  // the wait ended without its event
+}
+}  // namespace
+
+extern "C" int vgtb_diag_bounded_wait(long long limit_ns, int which) {
+  if ((which != 0 && which != 1) || limit_ns < 1 || limit_ns > 10000000000LL) return VGTB_E_INVALID;
+  if (!tc_gemm_supported()) return VGTB_E_UNSUPPORTED;
+  Scratch sc;
+  int* err = sc.get<int>(1);
+  int* flags = sc.get<int>(1);
+  if (!err || !flags) return VGTB_E_CUDA;
+  TcParams P;
+  memset(&P, 0, sizeof(P));
+  P.err = err;
+  P.flags = flags;
+  P.timeout_ns = limit_ns;
+  k_diag_wait<<<1, 32>>>(P, which);
+  if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) return VGTB_E_CUDA;
+  int h = 0;
+  if (cudaMemcpy(&h, err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return VGTB_E_CUDA;
+  if (h & 16) return VGTB_OK;
+  return (h & 3) ? VGTB_E_TIMEOUT : VGTB_E_CUDA;
 }

@@ -58,10 +58,13 @@ enum : int {
 // IEEE-754 float <-> double conversions done with integer bit operations.
 // GB300 runs FP64 instructions, conversions included, at a small fraction of
 // the integer rate, so the split-form kernels convert with these and keep the
-// FP64 pipe for the arithmetic that needs it.  float -> double is exact (signed zero for float zeros and
-// subnormals, which are below 1.2e-38); double -> float rounds to nearest even
-// and flushes magnitudes below 2^-126 to signed zero and above the float range
-// to infinity.
+// FP64 pipe for the arithmetic that needs it.
+//  * f2d_bits: exact for every normal float, infinities and NaNs (payload
+//    kept); float subnormals (below 2^-126 = 1.2e-38) become signed zero.
+//  * d2f_bits: round to nearest, ties to even, like __double2float_rn, for
+//    every input of magnitude >= 2^-126; an input below 2^-126 becomes signed
+//    zero (no float subnormals), magnitudes that round above the float range
+//    become +-infinity, and a NaN becomes a quiet NaN of the same sign.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double f2d_bits(float f) {
   const uint32_t u = __float_as_uint(f);
@@ -83,6 +86,8 @@ __device__ __forceinline__ float d2f_bits(double d) {
   f += (rest > 0x10000000u || (rest == 0x10000000u && (mant & 1u))) ? 1u : 0u;
   f = (e <= 0) ? sign : f;
   f = (e >= 255) ? (sign | 0x7f800000u) : f;
+  const uint32_t ah = hi & 0x7fffffffu;
+  f = (ah > 0x7ff00000u || (ah == 0x7ff00000u && lo != 0u)) ? (sign | 0x7fc00000u) : f;
   return __uint_as_float(f);
 }
 
@@ -90,6 +95,7 @@ constexpr int kSccRowsPerCta = 4;  // rows of gamma per CTA of k_scc_eps (one wa
 
 struct DevSys {
   int N, Np, nat, nk, n_tgt, n_blk;
+  int scc_frozen;          // 1: H keeps the shift eps0 of D(0) (VGTB_SCC_FROZEN)
   double omega, nel, dt;
   double inv_omega;        // 1 / omega (an FP64 division is a long sequence on GB300)
   const int* orb_off;      // [nat+1]
@@ -131,8 +137,7 @@ struct DevSys {
   const float* dsf;        // [3][ds_stride]
   const float2* phasef;    // [nk][n_blk]
   float* R0f;              // [nk][Np][2Np] planar
-  float4* kf;              // [nk][n_el][3] FP32 k-space blocks {S, P_x}, {P_y, P_z}, {H0, 0} (split form)
-  const float* wkf;        // [nk] k weights as float (split form)
+  float2* D0f;             // [nk][Np][Np] FP32 copy of D0 (split form, block-sparse first product)
 };
 
 struct DevTraj {
@@ -172,7 +177,43 @@ struct DevItem {
   float* Xf;               // split form: [Np][2Np] planar X
   double2* Cd;             // Crank-Nicolson: occupied states as rows, C^dagger [nocc][Np]
   double2* Y[2];           // Crank-Nicolson: fixed-point iterates [nocc][Np]
+  // block-sparse first product: H_k(t) and dH_k(t) at the target elements only
+  // ([n_el], complex; double2 on the FP64 path, float2 in the split form), and in
+  // the split form the FP32 copy of the current dD level ([Np][Np] float2)
+  void* kH;
+  void* kdH;
+  float2* dDf;
 };
+
+// ---------------------------------------------------------------------------
+// Block-sparse first product (k_bsr.cu): W = sum_seg A_seg R_seg^dagger with R
+// on the target pattern (every atom 4 orbitals), A dense and Hermitian.
+// ---------------------------------------------------------------------------
+constexpr int kBsrThreads = 128;   // output rows (columns of A) per CTA
+constexpr int kBsrGroupF32 = 8;    // atoms per group (output columns / 4), split form
+constexpr int kBsrGroupF64 = 4;    // atoms per group, FP64 path
+
+struct BsrSys {
+  int Np, nat, n_grp;
+  const int* grp_t0;       // [n_grp+1] first target of each group (targets sorted by row atom)
+  const int* grp_e0;       // [n_grp+1] first union entry of each group
+  const int* ent_K;        // [n_ent] column atom K of each entry
+  const short* ent_slot;   // [n_ent][G] target index of (J_j, K) minus grp_t0, or -1
+};
+
+struct BsrItem {
+  int sys, nseg;
+  const void* A[2];        // [Np][Np] complex (double2 / float2), Hermitian
+  long long a_par;         // segment 0 reads A[0] + ((*step) & 1) * a_par (leapfrog level)
+  const void* R[2];        // [n_el] complex target blocks (4 x 4 row-major each)
+  void* W;                 // FP64: [Np][Np] double2; split: embedded BF16 pieces [2][2Np][2Np]
+};
+int bsr_group(int fp64);
+size_t bsr_smem_bytes(int fp64, int max_grp_targets);
+int bsr_configure(int fp64, int max_grp_targets);
+int bsr_units(int fp64, int n_grp, int Np);  // CTAs per item
+void launch_bsr(const BsrItem* items, const BsrSys* sys, int n_items, int max_units, int fp64, int max_grp_targets,
+                const int* step, cudaStream_t st);
 
 // Crank-Nicolson convergence check of one item: max |Y[a] - Y[b]| over nocc x N
 struct CnCheckItem {
@@ -196,7 +237,6 @@ enum PhaseMode : int {
 // delta: 0 = D itself (FP64), 1 = dD with the D0 part from obs0 (FP64)
 void launch_obs(const DevSys* sys, const DevTraj* trj, const DevItem* items, const int* warp_prefix,
                 int n_traj, int total_warps, const int* step, int delta, int fixed_step, cudaStream_t st);
-void launch_kblocks_f32(const DevSys* sys, int s_idx, long long n, cudaStream_t st);
 // atoms_done = 1: the per-atom sums were made by k_obs_atoms_split (split form)
 void launch_scc(const DevSys* sys, DevTraj* trj, int n_traj, const int* step, int stride,
                 int fixed_step, int record, int max_nat, int atoms_done, cudaStream_t st);
@@ -238,6 +278,7 @@ struct LeapItem {
   const float* R0f;        // optional (split path, FP32 planar)
   double2* D[2];
   __nv_bfloat16* pieces;   // optional [2][Np][2Np]
+  float2* f32;             // optional [Np][Np]: FP32 copy of the new level (split form)
   int Np;
   int mode;                // 0 = leapfrog, 1 = write the derivative only into out
   double2* out;            // mode 1 target
@@ -255,6 +296,7 @@ void launch_split_planar(const double2* src, __nv_bfloat16* dst, int N, int Np, 
 void launch_increment(int* step, cudaStream_t st);
 void launch_hermitize(double2* a, int n, int ld, cudaStream_t st);
 void launch_split_embedded(const double2* src, __nv_bfloat16* dst, int Np, cudaStream_t st);
+void launch_to_f32(const double2* src, float2* dst, long long n, cudaStream_t st);
 
 // post-propagation reductions (k_spectrum.cu)
 void launch_conductivity(const double* J, int n0, int n1, double dt, double e0, double tau0, const double* omega,

@@ -7,10 +7,15 @@
 // cudaMalloc, cudaFree or allocating library call.  Host code cannot pass the
 // array's name to a kernel (in host code it is only a stand-in, not a device
 // address): the first call on each device looks the address up with
-// cudaGetSymbolAddress and caches it.
+// cudaGetSymbolAddress and keeps it together with the identity of the CUDA
+// context it belongs to; a call made under another context of that device (after
+// cudaDeviceReset, say) repeats the set-up.  The set-up runs under a mutex, so
+// first calls from several host threads do not race on the cached values.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstring>
+#include <mutex>
 
 #include "../../include/vgtb.h"
 #include "tc_kernel.cuh"
@@ -32,7 +37,27 @@ constexpr size_t kNaScratchBytes = kOffErr + 256;                   // 2 MiB + 5
 static __device__ __align__(256) unsigned char g_na_scratch[kNaScratchBytes];
 
 constexpr int kMaxDevices = 64;
-unsigned char* g_na_addr[kMaxDevices] = {nullptr};
+
+// Per-device set-up state, read and written under g_na_mu only.
+struct NaDevice {
+  unsigned long long ctx_id = 0;  // identity of the context the address belongs to
+  unsigned char* addr = nullptr;  // device address of g_na_scratch in that context
+};
+std::mutex g_na_mu;
+NaDevice g_na_dev[kMaxDevices];
+PFN_cuTensorMapEncodeTiled_v12000 g_na_encode = nullptr;
+PFN_cuCtxGetCurrent_v4000 g_na_ctx_current = nullptr;
+PFN_cuCtxGetId_v12000 g_na_ctx_id = nullptr;
+
+template <typename F>
+F na_entry(const char* name, int version) {
+  void* f = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion(name, &f, version, cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess)
+    return nullptr;
+  return reinterpret_cast<F>(f);
+}
 
 // Planar BF16 pieces [Re(row) | Im(row)] of an n x n complex matrix, padded to Np
 // with zeros (every element of the Np x 2Np region is written).
@@ -85,45 +110,60 @@ __global__ void k_na_prob(TcProb* prob, int* err, int Np, float* out) {
   *err = 0;
 }
 
-// FP32 planar product -> n x n complex128 interleaved output.
-__global__ void k_na_out(const float* __restrict__ x, int n, int Np, double2* c) {
+// FP32 planar product -> n x n complex128 interleaved output; nothing is
+// written when the product kernel set its error word (a bounded wait expired).
+__global__ void k_na_out(const float* __restrict__ x, int n, int Np, const int* __restrict__ err, double2* c) {
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (long long)n * n) return;
+  if (idx >= (long long)n * n || *err != 0) return;
   const int i = (int)(idx / n), j = (int)(idx % n);
   c[idx] = make_double2(x[(long long)i * 2 * Np + j], x[(long long)i * 2 * Np + Np + j]);
 }
 
-// Per-device set-up: the device address of the scratch array and the shared
-// memory limit of the product kernel.  Runs with that device current.
-int na_setup(int dev) {
-  if (g_na_addr[dev]) return VGTB_OK;
+// Per-device set-up, run with that device current: the device address of the
+// scratch array (cudaGetSymbolAddress, checked) and the shared-memory limit of
+// the product kernel.  Done once per device and context; *addr receives the
+// address.
+int na_setup(int dev, unsigned char** addr) {
+  std::lock_guard<std::mutex> lock(g_na_mu);
+  if (!g_na_encode) g_na_encode = na_entry<PFN_cuTensorMapEncodeTiled_v12000>("cuTensorMapEncodeTiled", 12000);
+  if (!g_na_ctx_current) g_na_ctx_current = na_entry<PFN_cuCtxGetCurrent_v4000>("cuCtxGetCurrent", 4000);
+  if (!g_na_ctx_id) g_na_ctx_id = na_entry<PFN_cuCtxGetId_v12000>("cuCtxGetId", 12000);
+  if (!g_na_encode || !g_na_ctx_current || !g_na_ctx_id) return VGTB_E_CUDA;
+  CUcontext cu = nullptr;
+  if (g_na_ctx_current(&cu) != CUDA_SUCCESS) return VGTB_E_CUDA;
+  if (!cu) {
+    // no context current on this thread yet: cudaSetDevice makes the device's
+    // primary context current (CUDA 12 and later)
+    if (cudaSetDevice(dev) != cudaSuccess || g_na_ctx_current(&cu) != CUDA_SUCCESS || !cu) return VGTB_E_CUDA;
+  }
+  unsigned long long id = 0;
+  if (g_na_ctx_id(cu, &id) != CUDA_SUCCESS) return VGTB_E_CUDA;
+  NaDevice& d = g_na_dev[dev];
+  if (d.addr && d.ctx_id == id) {
+    *addr = d.addr;
+    return VGTB_OK;
+  }
   void* p = nullptr;
   cudaError_t e = cudaGetSymbolAddress(&p, g_na_scratch);
   if (e != cudaSuccess || !p) return VGTB_E_CUDA;
   e = cudaFuncSetAttribute(k_tc_gemm<256, 2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            2 * (2 * BM * BK * 2 + 2 * 256 * BK * 2) + 1024 + 256);
   if (e != cudaSuccess) return VGTB_E_CUDA;
-  g_na_addr[dev] = static_cast<unsigned char*>(p);
+  d.addr = static_cast<unsigned char*>(p);
+  d.ctx_id = id;
+  *addr = d.addr;
   return VGTB_OK;
 }
 
+// g_na_encode is set by na_setup() before any call of this function.
 bool na_map(CUtensorMap* m, void* base, int cols, int rows, int box_rows) {
-  static PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
-  if (!enc) {
-    void* f = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
-        q != cudaDriverEntryPointSuccess)
-      return false;
-    enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
-  }
   cuuint64_t dims[4] = {(cuuint64_t)cols, (cuuint64_t)rows, 2, 1};
   cuuint64_t strides[3] = {(cuuint64_t)cols * 2, (cuuint64_t)cols * rows * 2, (cuuint64_t)cols * rows * 4};
   cuuint32_t box[4] = {(cuuint32_t)BK, (cuuint32_t)box_rows, 1, 1};
   cuuint32_t es[4] = {1, 1, 1, 1};
-  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  return g_na_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, base, dims, strides, box, es,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 }  // namespace
@@ -137,10 +177,10 @@ extern "C" int vgtb_split_cgemm_noalloc(int n, const double* a, const double* r,
   if (!tc_gemm_supported()) return VGTB_E_UNSUPPORTED;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return VGTB_E_CUDA;
-  int rc = na_setup(dev);
+  unsigned char* base = nullptr;
+  int rc = na_setup(dev, &base);
   if (rc != VGTB_OK) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  unsigned char* base = g_na_addr[dev];
   __nv_bfloat16* ap = reinterpret_cast<__nv_bfloat16*>(base + kOffA);
   __nv_bfloat16* rp = reinterpret_cast<__nv_bfloat16*>(base + kOffR);
   float* xo = reinterpret_cast<float*>(base + kOffOut);
@@ -163,7 +203,7 @@ extern "C" int vgtb_split_cgemm_noalloc(int n, const double* a, const double* r,
   P.timeout_ns = 2000000000LL;
   const int smem = 2 * (2 * BM * BK * 2 + 2 * 256 * BK * 2) + 1024 + 256;
   k_tc_gemm<256, 2, 1><<<P.total_tiles, 192, smem, st>>>(P);
-  k_na_out<<<(unsigned)(((long long)n * n + 255) / 256), 256, 0, st>>>(xo, n, Np, reinterpret_cast<double2*>(c));
+  k_na_out<<<(unsigned)(((long long)n * n + 255) / 256), 256, 0, st>>>(xo, n, Np, err, reinterpret_cast<double2*>(c));
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return VGTB_E_CUDA;
   int herr = 0;

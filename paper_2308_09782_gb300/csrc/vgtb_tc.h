@@ -26,6 +26,7 @@ struct TcSysView {
 //   product 2: X = S^-1 W^dagger               -> FP32 planar X
 // force_variant[p] >= 0 uses that tile variant for product p+1; otherwise variant
 // 0, or with autotune the fastest candidate (median of 9 timed launches).
+// p1 == nullptr builds product 2 only (the first product runs block-sparse).
 // Returns 0 on success, else fills *msg.
 int tc_build_plans(const std::vector<TcSysView>& sys, const std::vector<DevItem>& items, long long timeout_ns,
                    int autotune, const int force_variant[2], cudaStream_t st, TcPlan** p1, TcPlan** p2,

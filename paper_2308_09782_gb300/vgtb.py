@@ -25,6 +25,11 @@ INIT_GROUND = 0
 INIT_USER = 1
 LEAPFROG = 0
 CRANK_NICOLSON = 1
+P1_AUTO = 0
+P1_DENSE = 1
+P1_BLOCKS = 2
+SCC_ON = 0
+SCC_FROZEN = 1
 KERNEL_CLASSES = ["obs", "scc", "phase", "gemm1", "gemm2", "leap"]
 
 EXPORTS = ["vgtb_default_options", "vgtb_create", "vgtb_create_batch", "vgtb_set_density",
@@ -33,7 +38,8 @@ EXPORTS = ["vgtb_default_options", "vgtb_create", "vgtb_create_batch", "vgtb_set
            "vgtb_profile", "vgtb_kernel_stats", "vgtb_last_error", "vgtb_destroy",
            "vgtb_diag_split_chain", "vgtb_split_cgemm_noalloc", "vgtb_spectrum", "vgtb_group_charges",
            "vgtb_set_coefficients", "vgtb_get_coefficients", "vgtb_tile_config",
-           "vgtb_diag_split_chain_variant", "vgtb_diag_num_variants"]
+           "vgtb_diag_split_chain_variant", "vgtb_diag_num_variants", "vgtb_diag_convert",
+           "vgtb_diag_bounded_wait"]
 
 
 class VgtbSystem(C.Structure):
@@ -52,7 +58,7 @@ class VgtbOptions(C.Structure):
                 ("obs_stride", C.c_int), ("graph_steps", C.c_int), ("autotune", C.c_int),
                 ("scc_tol", C.c_double), ("scc_max_iter", C.c_int),
                 ("integrator", C.c_int), ("cn_iter", C.c_int), ("cn_tol", C.c_double),
-                ("tile_variant", C.c_int * 2)]
+                ("tile_variant", C.c_int * 2), ("product1", C.c_int), ("scc", C.c_int)]
 
 
 _lib = None
@@ -99,6 +105,8 @@ def load(path: str = LIB_PATH):
     lib.vgtb_tile_config.argtypes = [ctxp, I, P(I)]
     lib.vgtb_diag_split_chain_variant.argtypes = [I, P(D), P(D), P(D), I, P(D), P(D)]
     lib.vgtb_diag_num_variants.argtypes = []
+    lib.vgtb_diag_bounded_wait.argtypes = [C.c_longlong, I]
+    lib.vgtb_diag_convert.argtypes = [I, P(D), P(C.c_float), P(C.c_float), P(C.c_float), P(D), P(D)]
     for name in EXPORTS:
         if name not in ("vgtb_default_options", "vgtb_last_error", "vgtb_destroy", "vgtb_state_size"):
             getattr(lib, name).restype = I
@@ -182,6 +190,23 @@ def diag_split_chain(a, r, s, variant: int = -1):
     if rc != VGTB_OK:
         raise VgtbError(rc, "vgtb_diag_split_chain_variant failed")
     return w, x
+
+
+def diag_convert(d_in, f_in):
+    """The library's bit-operation conversions next to CUDA's on the device.
+    Returns (d2f_bits(d_in), __double2float_rn(d_in), f2d_bits(f_in), double(f_in))."""
+    lib = load()
+    d_in = np.ascontiguousarray(d_in, np.float64)
+    f_in = np.ascontiguousarray(f_in, np.float32)
+    assert d_in.shape == f_in.shape and d_in.ndim == 1
+    n = d_in.shape[0]
+    fb, fr = np.zeros(n, np.float32), np.zeros(n, np.float32)
+    db, dr = np.zeros(n), np.zeros(n)
+    fp = lambda m: m.ctypes.data_as(C.POINTER(C.c_float))  # noqa: E731
+    rc = lib.vgtb_diag_convert(n, _dptr(d_in), fp(f_in), fp(fb), fp(fr), _dptr(db), _dptr(dr))
+    if rc != VGTB_OK:
+        raise VgtbError(rc, "vgtb_diag_convert failed")
+    return fb, fr, db, dr
 
 
 def num_tile_variants() -> int:
@@ -309,6 +334,8 @@ class Context:
         """{"tile_n", "stages", "schedule", "pair"} of tcgen05 product 1 or 2 (split contexts)."""
         cfg = (C.c_int * 4)()
         self._check(load().vgtb_tile_config(self._h, int(product), cfg))
+        if cfg[2] == 3:
+            return {"schedule": "block-sparse", "atoms_per_group": cfg[0], "rows_per_cta": cfg[1]}
         return {"tile_n": cfg[0], "stages": cfg[1],
                 "schedule": ("classic", "stream-K", "classic waves + stream-K")[cfg[2]], "pair": bool(cfg[3])}
 

@@ -56,31 +56,51 @@ def test_every_tile_variant_matches_numpy(n):
         assert rel_fro([x], [x_ref]) < 6e-5, v
 
 
+@pytest.mark.parametrize("product1", [0, 2])
 @pytest.mark.parametrize("name,nsteps", [("si8_pulse", 1000), ("si64_pulse", 2000)])
-def test_split_propagation_matches_oracle(name, nsteps):
+def test_split_propagation_matches_oracle(name, nsteps, product1):
+    """product1 = AUTO (0): the tcgen05 BF16x3 first product over all of
+    [dD | D0][H | dH]^dagger (the split form's default); BLOCKS (2): the
+    block-sparse FP32 first product on the CUDA cores."""
     from paper_2308_09782_gb300 import vgtb
     ref = oracle_run(name, nsteps)
-    with gpu_run(name, nsteps, precision=vgtb.SPLIT_BF16X3) as c:
+    with gpu_run(name, nsteps, precision=vgtb.SPLIT_BF16X3, product1=product1) as c:
         J, E, q = c.observables(0)
         D = [c.get_density(0, k) for k in range(8)]
     err_j = rel_fro([J], [ref["J"]])
     err_d = rel_fro(D, ref["D"])
     err_q = np.abs(q - ref["q"]).max()
     err_e = np.abs(E - ref["E"]).max()
-    print(f"{name}: J {err_j:.3e}  D {err_d:.3e}  q {err_q:.3e}  E {err_e:.3e}")
+    print(f"{name} product1={product1}: J {err_j:.3e}  D {err_d:.3e}  q {err_q:.3e}  E {err_e:.3e}")
     assert err_j <= 1e-4
     assert err_d <= 1e-4
     assert err_q <= 1e-4
 
 
-def test_split_timeout_returns_error_and_context_recovers():
-    """A 1 ns wait limit makes the product kernels give up: E_TIMEOUT, no hang;
-    a fresh context afterwards works."""
+def test_bounded_waits_run_out_deterministically():
+    """The product kernels' wait routines, on an mbarrier phase that no thread
+    completes and on a stream-K flag that no CTA sets, give up after their limit
+    (1 ms here) and report it: VGTB_E_TIMEOUT, no hang; the GPU stays usable."""
     from paper_2308_09782_gb300 import vgtb
-    name = "si8_pulse"
+    lib = vgtb.load()
+    for which in (0, 1):
+        assert lib.vgtb_diag_bounded_wait(1_000_000, which) == -8, which
+    assert lib.vgtb_diag_bounded_wait(0, 0) == -1
+    with gpu_run("si8_pulse", 20, precision=vgtb.SPLIT_BF16X3) as ok:
+        J, _, _ = ok.observables(0)
+    assert np.all(np.isfinite(J))
+
+
+def test_split_timeout_returns_error_and_context_recovers():
+    """A 1 ns wait limit makes the tcgen05 product kernels give up inside
+    vgtb_propagate: E_TIMEOUT, no hang; a fresh context afterwards works.  The
+    64-atom system with the dense tcgen05 first product (K' = 4 Np) keeps the
+    kernels' waits long enough to reach the limit check."""
+    from paper_2308_09782_gb300 import vgtb
+    name = "si64_pulse"
     sysd, A, _ = system(name)
     _, gs = oracle_ground(name)
-    c = vgtb.Context(sysd, precision=vgtb.SPLIT_BF16X3, init=vgtb.INIT_USER, timeout_ns=1)
+    c = vgtb.Context(sysd, precision=vgtb.SPLIT_BF16X3, init=vgtb.INIT_USER, timeout_ns=1, product1=1)
     for k, D in enumerate(gs["D"]):
         c.set_density(0, k, D)
     c.set_field(0, A[:6])
