@@ -36,6 +36,7 @@ CONFIG = "si512_kick"
 WORKLOAD = ("512-atom Si supercell (diamond 4x4x4, sigma=0.3 bohr), sp3, N=2048 orbitals, Gamma, "
             "kick A_x=0.001 au, dt=0.2 au, SCC on")
 AU_FS = 0.0241888432658
+P1 = {"auto": 0, "dense": 1, "blocks": 2}     # vgtb_options.product1
 
 
 def parse():
@@ -56,6 +57,8 @@ def parse():
                    help="steps per window of the three steady-state windows timed after the headline (0 = skip)")
     p.add_argument("--batched-steps", type=int, default=100,
                    help="timed steps of the batched form inside the headline run (0 = skip)")
+    p.add_argument("--product1", choices=["auto", "dense", "blocks"], default="auto",
+                   help="form of the split path's first product (vgtb_options.product1)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--cpu-1thread-steps", type=int, default=1,
@@ -262,7 +265,7 @@ def hbm_rates(sysd, Np, kern_ms, peak_gbs, sparse=True):
     nat = len(norb)
     nk = len(sysd["wk"])
     byts = {
-        "leap": 56 * Np * Np,                                        # X, R0 f32; dD r/w f64; f32 copy or pieces
+        "leap": 48 * Np * Np,                                        # X f32 (R0 folded in); dD r/w f64; f32 copy or pieces
         # S, H0, dS f32 per image; out: H and dH at the nonzeros (2 x float2) or embedded BF16 pieces (16 x 2 B)
         "phase": nk * (20 * el_img + 8 * len(blk) + (16 if sparse else 32) * n_el),
         "obs": nk * 96 * n_el + 40 * nat,                            # dD f64 + S, P, H0 blocks f64
@@ -398,7 +401,7 @@ def native(args):
     if args.tiles != "auto":
         tile_opts = {"autotune": 0, "tile_variant": [int(x) for x in args.tiles.split(",")]}
     ctx = vgtb.Context(sysd, precision=vgtb.SPLIT_BF16X3, init=vgtb.INIT_GROUND,
-                       cuda_stream=stream.cuda_stream, graph_steps=50, **tile_opts)
+                       cuda_stream=stream.cuda_stream, graph_steps=50, product1=P1[args.product1], **tile_opts)
     ctx.set_field(0, A[:n_need])
     tiles = {f"product{p}": ctx.tile_config(p) for p in (1, 2)}
     tiles["choice"] = ("autotuned at create: fastest of the tcgen05 tile variants (median of 9 launches)"
@@ -544,7 +547,7 @@ def native(args):
         "warmup": W, "ms_per_step": round(step_ms, 4), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16x3 (f32 accumulate) + f64 master", "data": "synthetic",
         "config": {"workload": WORKLOAD, "name": CONFIG, "precision": "split_bf16x3 delta form",
-                   "tiles": tiles,
+                   "product1": args.product1, "tiles": tiles,
                    "parallelism": f"{world} independent replica(s)",
                    "l2": "working set ~0.6 GB per step, larger than the 129 MB L2 (no flush)",
                    "fs_per_hour": round(value / world * 0.2 * AU_FS * 3600, 2)},
@@ -697,7 +700,8 @@ def run_batched(args, K, W, timing_start=False):
         tile_opts = {"autotune": 0, "tile_variant": [int(x) for x in args.tiles.split(",")]}
     ctx = vgtb.Context(systems, traj_sys=traj_sys, precision=vgtb.SPLIT_BF16X3,
                        init=vgtb.INIT_USER if timing_start else vgtb.INIT_GROUND,
-                       cuda_stream=stream.cuda_stream, graph_steps=20, obs_stride=10, **tile_opts)
+                       cuda_stream=stream.cuda_stream, graph_steps=20, obs_stride=10, product1=P1[args.product1],
+                       **tile_opts)
     if timing_start:
         for si, sd in enumerate(systems):
             n = int(sd["orb_offset"][-1])

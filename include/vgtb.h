@@ -115,13 +115,15 @@ typedef struct {
   int tile_variant[2];      /* split form: tile variant of product 1 / product 2 (see
                                vgtb_tile_config; -1 = variant 0, or the autotuner's choice) */
   int product1;             /* form of the first product W = D H of Eq. 6 (VGTB_P1_*):
-                               AUTO (0, default): the FP64 path runs it block-sparse, the split
-                               form as the dense tcgen05 GEMM (the faster form at 512 atoms);
+                               AUTO (0, default): the FP64 path runs it block-sparse (below); the
+                               split form runs the tcgen05 GEMM and skips the 64-wide k-panels in
+                               which a tile's rows of H_k and dH_k are zero;
                                DENSE: a dense GEMM over all of H_k (8 N^3 flops; FP64 DFMA or
-                               tcgen05 BF16x3); BLOCKS: block-sparse over the nonzero atom blocks
-                               of H_k on the CUDA cores (8 nnz(H) N flops; FP64, or FP32 in the
-                               split form), which needs every atom to carry 4 orbitals (AUTO
-                               falls back to DENSE otherwise, BLOCKS fails with E_UNSUPPORTED) */
+                               tcgen05 BF16x3, no panel skipped); BLOCKS: block-sparse over the
+                               nonzero atom blocks of H_k on the CUDA cores (8 nnz(H) N flops;
+                               FP64, or FP32 in the split form), which needs every atom to carry
+                               4 orbitals (the FP64 AUTO falls back to DENSE otherwise, BLOCKS
+                               fails with E_UNSUPPORTED) */
   int scc;                  /* VGTB_SCC_ON (0, default): the shift eps = gamma dq of Eq. 10 follows
                                the charges at every step; VGTB_SCC_FROZEN: H keeps the shift of
                                D_k(0) at every step (non-self-consistent propagation); charges,
@@ -249,9 +251,10 @@ int vgtb_kernel_stats(vgtb_ctx* ctx, long long* launches, double* ms, int n);
  * (product 1 = [dD|D0][H|dH]^dagger, product 2 = S^-1 W^dagger), chosen at
  * create (variant 0, or the autotuner's fastest).  cfg[4] = {tile width,
  * pipeline stages, schedule (0 classic, 1 stream-K, 2 whole waves classic and
- * stream-K over the rest), 1 if the tile spans a 2-SM CTA pair}.  When the first
- * product runs block-sparse (VGTB_P1_BLOCKS), product 1 reports {atoms per group,
- * output rows per CTA, 3, 0}.
+ * stream-K over the rest; 4, 5, 6: the same with the k-panels skipped in which
+ * the tile's rows of H_k and dH_k are zero, product 1 only), 1 if the tile spans
+ * a 2-SM CTA pair}.  When the first product runs block-sparse
+ * (VGTB_P1_BLOCKS), product 1 reports {atoms per group, output rows per CTA, 3, 0}.
  * Errors: E_INVALID (product not 1 or 2, NULL), E_STATE (FP64 context). */
 int vgtb_tile_config(const vgtb_ctx* ctx, int product, int* cfg);
 

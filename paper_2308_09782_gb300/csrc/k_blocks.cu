@@ -238,27 +238,63 @@ __device__ __forceinline__ float half_sum_f(float v) {
 
 // ---------------------------------------------------------------------------
 // k_obs_atoms_split: the split form's observables and per-atom sums in one
-// launch.  One CTA per (trajectory, atom I); its threads take the nonzeros of
-// the atom's rows (all targets (I, J)) and form the dD sums in FP64 from the
-// FP64 master dD and the FP64 k-space blocks (S_k, P_k, H0_k), so charges,
-// current and energy keep the precision of the master copy; the 8 warp sums,
-// the constant D0 part (obs0a) and the A terms (both linear in the sums) are
-// added in FP64 too.  Warp 0 writes dq_I, q_I and the atom's shares of T and of
-// the band energy, as k_scc_atoms does for the FP64 paths.  The k loop is
-// outside the element loop so that each k's sums take its weight once.
+// launch.  One CTA of 4 warps per (trajectory, atom I); its threads take the
+// nonzeros of the atom's rows (all targets (I, J), ~490 for an sp3 atom, so at
+// most a few per thread, whose loads are issued together) and form the dD
+// sums in FP64 from the FP64 master dD and the FP64 k-space blocks (S_k, P_k,
+// H0_k), so charges, current and energy keep the precision of the master copy.
+// Each warp reduces its five sums with one reduce-scatter (nine FP64 additions
+// per lane: GB300 issues FP64 warp instructions at a small fraction of the FP32
+// rate whatever the number of active lanes), thread 0 adds the warps, the
+// constant D0 part (obs0a) and the A terms (both linear in the sums) and writes
+// dq_I, q_I and the atom's shares of T and of the band energy, as k_scc_atoms
+// does for the FP64 paths.
 // ---------------------------------------------------------------------------
-// 256 threads: two passes over the ~490 nonzeros of an sp3 atom's row block, and
-// every CTA of a 512-atom step resident in one wave
-constexpr int kObsAtomThreads = 256;
+constexpr int kObsThreads = 128;
+constexpr int kObsChunk = 4;  // nonzeros per thread whose loads are issued together
 
-__global__ void __launch_bounds__(kObsAtomThreads) k_obs_atoms_split(const DevSys* __restrict__ sysv, DevTraj* trj,
-                                                                   const DevItem* __restrict__ items, int n_traj,
-                                                                   int max_nat, const int* __restrict__ step,
-                                                                   int stride, int fixed_step, int record) {
+// Reduce-scatter of eight per-lane values over a warp: afterwards lane l holds
+// the warp total of value (l >> 2) & 7 (every lane of a group of four holds the
+// same total).  Nine FP64 additions per lane instead of the 5 x 5 of five
+// butterflies.
+__device__ __forceinline__ double warp_reduce_scatter8(double (&v)[8], int lane) {
+  // xor 16: keep values 0-3 (lower half-warp) or 4-7 (upper), add the partner's copy of them
+  const bool up16 = lane & 16;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const double send = up16 ? v[i] : v[i + 4];
+    const double keep = up16 ? v[i + 4] : v[i];
+    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+  // xor 8: keep 2 of the 4
+  const bool up8 = lane & 8;
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const double send = up8 ? v[i] : v[i + 2];
+    const double keep = up8 ? v[i + 2] : v[i];
+    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  // xor 4: keep 1 of the 2
+  const bool up4 = lane & 4;
+  {
+    const double send = up4 ? v[0] : v[1];
+    const double keep = up4 ? v[1] : v[0];
+    v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  }
+  // lanes with the same bits 4..2 hold the same value: finish over bits 1, 0
+  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 2);
+  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+  return v[0];
+}
+
+__global__ void __launch_bounds__(kObsThreads, 4) k_obs_atoms_split(const DevSys* __restrict__ sysv, DevTraj* trj,
+                                                               const DevItem* __restrict__ items, int n_traj,
+                                                               int max_nat, const int* __restrict__ step, int stride,
+                                                               int fixed_step, int record) {
   pdl_wait();
   pdl_trigger();
-  constexpr int NW = kObsAtomThreads / 32;
-  __shared__ double red[5][NW];
+  constexpr int NW = kObsThreads / 32;
+  __shared__ double s_tot[NW][5];
   const int t = blockIdx.x / max_nat, I = blockIdx.x % max_nat;
   if (t >= n_traj) return;
   DevTraj& T = trj[t];
@@ -267,54 +303,55 @@ __global__ void __launch_bounds__(kObsAtomThreads) k_obs_atoms_split(const DevSy
   const int n = fixed_step >= 0 ? fixed_step : *step;
   const int par = n & 1;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  double sS = 0.0, sx = 0.0, sy = 0.0, sz = 0.0, sH = 0.0;
+  double v[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};  // S, P_x, P_y, P_z, H0 sums (3 slots unused)
   // the atom's nonzeros are contiguous (targets sorted by row atom); el_off gives
-  // each one's offset in the Np x Np matrix, so a thread needs no index lookups
+  // each one's offset in the Np x Np matrix
   const int e0 = S.el_atom0[I], e1 = S.el_atom0[I + 1];
   const long long ps = (long long)S.nk * S.n_el;
   for (int k = 0; k < S.nk; ++k) {
     const double2* Dk = items[T.item0 + k].D[par];
-    double cS = 0.0, cx = 0.0, cy = 0.0, cz = 0.0, cH = 0.0;
-    for (int e = e0 + threadIdx.x; e < e1; e += kObsAtomThreads) {
-      const double2 dd = Dk[S.el_off[e]];
-      const long long ke = (long long)k * S.n_el + e;
-      const double2 bs = S.kS[ke], bx = S.kP[ke], by = S.kP[ps + ke], bz = S.kP[2 * ps + ke], bh = S.kH0[ke];
-      // Re(dD conj(X)) for X = S_k, P_k^x, P_k^y, P_k^z, H0_k
-      cS = fma(dd.x, bs.x, fma(dd.y, bs.y, cS));
-      cx = fma(dd.x, bx.x, fma(dd.y, bx.y, cx));
-      cy = fma(dd.x, by.x, fma(dd.y, by.y, cy));
-      cz = fma(dd.x, bz.x, fma(dd.y, bz.y, cz));
-      cH = fma(dd.x, bh.x, fma(dd.y, bh.y, cH));
+    const long long kb = (long long)k * S.n_el;
+    double c[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int eb = e0; eb < e1; eb += kObsThreads * kObsChunk) {
+      int ee[kObsChunk];
+      bool ok[kObsChunk];
+      double2 d[kObsChunk];
+#pragma unroll
+      for (int u = 0; u < kObsChunk; ++u) {
+        const int e = eb + threadIdx.x + kObsThreads * u;
+        ok[u] = e < e1;
+        ee[u] = ok[u] ? e : e0;
+      }
+#pragma unroll
+      for (int u = 0; u < kObsChunk; ++u) d[u] = ok[u] ? Dk[S.el_off[ee[u]]] : make_double2(0.0, 0.0);
+#pragma unroll
+      for (int u = 0; u < kObsChunk; ++u) {
+        const long long x = kb + ee[u];
+        const double2 bs = S.kS[x], bx = S.kP[x], by = S.kP[ps + x], bz = S.kP[2 * ps + x], bh = S.kH0[x];
+        // Re(dD conj(X)) for X = S_k, P_k^x, P_k^y, P_k^z, H0_k
+        c[0] = fma(d[u].x, bs.x, fma(d[u].y, bs.y, c[0]));
+        c[1] = fma(d[u].x, bx.x, fma(d[u].y, bx.y, c[1]));
+        c[2] = fma(d[u].x, by.x, fma(d[u].y, by.y, c[2]));
+        c[3] = fma(d[u].x, bz.x, fma(d[u].y, bz.y, c[3]));
+        c[4] = fma(d[u].x, bh.x, fma(d[u].y, bh.y, c[4]));
+      }
     }
     const double w = S.wk[k];
-    sS = fma(w, cS, sS);
-    sx = fma(w, cx, sx);
-    sy = fma(w, cy, sy);
-    sz = fma(w, cz, sz);
-    sH = fma(w, cH, sH);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) v[i] = fma(w, c[i], v[i]);
   }
-  sS = warp_sum(sS);
-  sx = warp_sum(sx);
-  sy = warp_sum(sy);
-  sz = warp_sum(sz);
-  sH = warp_sum(sH);
-  if (lane == 0) {
-    red[0][warp] = sS;
-    red[1][warp] = sx;
-    red[2][warp] = sy;
-    red[3][warp] = sz;
-    red[4][warp] = sH;
-  }
+  const double tot = warp_reduce_scatter8(v, lane);
+  const int slot = (lane >> 2) & 7;
+  if ((lane & 3) == 0 && slot < 5) s_tot[warp][slot] = tot;
   __syncthreads();
-  if (threadIdx.x >= 32) return;
-  const int l = threadIdx.x;
-  double v[5];
+  if (threadIdx.x != 0) return;
+  double r[5];
 #pragma unroll
-  for (int i = 0; i < 5; ++i) v[i] = warp_sum(l < NW ? red[i][l] : 0.0);
-  if (l != 0) return;
-  const double* o = S.obs0a + 5LL * I;
-#pragma unroll
-  for (int i = 0; i < 5; ++i) v[i] += o[i];
+  for (int i = 0; i < 5; ++i) {
+    double a = S.obs0a[5LL * I + i];
+    for (int w2 = 0; w2 < NW; ++w2) a += s_tot[w2][i];
+    r[i] = a;
+  }
   double A0 = 0.0, A1 = 0.0, A2 = 0.0;
   if (T.A) {
     A0 = T.A[3 * n];
@@ -324,19 +361,19 @@ __global__ void __launch_bounds__(kObsAtomThreads) k_obs_atoms_split(const DevSy
   constexpr double ic = 1.0 / kLight;
   const double a0 = A0 * ic, a1 = A1 * ic, a2 = A2 * ic;
   const double alpha = 0.5 * (a0 * a0 + a1 * a1 + a2 * a2);
-  T.dq[I] = v[0] - S.z[I];
-  if (record && T.q && n % stride == 0) T.q[(long long)(n / stride) * S.nat + I] = v[0];
+  T.dq[I] = r[0] - S.z[I];
+  if (record && T.q && n % stride == 0) T.q[(long long)(n / stride) * S.nat + I] = r[0];
   double* ap = T.apart + 4LL * I;
-  ap[0] = v[1] + a0 * v[0];
-  ap[1] = v[2] + a1 * v[0];
-  ap[2] = v[3] + a2 * v[0];
-  ap[3] = v[4] + (a0 * v[1] + a1 * v[2] + a2 * v[3]) + alpha * v[0];
+  ap[0] = r[1] + a0 * r[0];
+  ap[1] = r[2] + a1 * r[0];
+  ap[2] = r[3] + a2 * r[0];
+  ap[3] = r[4] + (a0 * r[1] + a1 * r[2] + a2 * r[3]) + alpha * r[0];
 }
 
 void launch_obs_atoms_split(const DevSys* sys, DevTraj* trj, const DevItem* items, int n_traj, int max_nat,
                             const int* step, int stride, int fixed_step, int record, cudaStream_t st) {
-  launch_pdl(k_obs_atoms_split, n_traj * max_nat, kObsAtomThreads, 0, st, sys, trj, items, n_traj, max_nat, step,
-             stride, fixed_step, record);
+  launch_pdl(k_obs_atoms_split, n_traj * max_nat, kObsThreads, 0, st, sys, trj, items, n_traj, max_nat, step, stride,
+             fixed_step, record);
 }
 
 void launch_obs(const DevSys* sys, const DevTraj* trj, const DevItem* items, const int* warp_prefix,

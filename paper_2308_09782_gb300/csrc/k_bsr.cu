@@ -27,8 +27,10 @@
 // once; for each K the four rows of A are loaded once and applied to every J of
 // the group that has the block (J, K) (uniform branches: every thread of the
 // CTA sees the same K).  Accumulation is in registers.  k_bsr (one output row
-// per thread, 4 atoms per group) serves the FP64 path; k_bsr_f32x2 (below) the
+// per thread, 4 atoms per group) serves the FP64 path; k_bsr_f32p (below) the
 // split form.
+#include <algorithm>
+
 #include "vgtb_internal.h"
 
 namespace vgtb {
@@ -205,116 +207,134 @@ __global__ void __launch_bounds__(kBsrThreads) k_bsr(const BsrItem* __restrict__
 }
 
 // ---------------------------------------------------------------------------
-// Split form (FP32): the same product with two output rows per thread and the
-// group's 8 atoms split between two warp groups of 4 warps (4 atoms each).
-// A thread reads its two columns of each A row as one float4 (a warp reads 512
-// contiguous bytes per row), so every block (J, K) value it loads from shared
-// memory feeds 2 x 4 complex multiply-adds, and the A rows of an entry, loaded
-// by both warp groups, are shared through L1.  Loads run one entry ahead.
+// Split form (FP32), persistent: k_bsr_f32p.  A CTA of 128 threads takes
+// units (item, group of 8 atoms, chunk of 128 A columns) from a global counter
+// until none is left; one thread owns one column of A (one row of W) and the
+// 8 x 4 complex accumulators of the group's atoms.  Each thread stages its own
+// four A values of an entry through a ring of kBsrStages shared-memory slots
+// with cp.async (no other thread reads them, so no CTA barrier is needed per
+// entry), so kBsrStages - 1 entries are in flight while one is applied; the
+// ring runs on across the segment boundary.  The R blocks of the group's current
+// segment sit in shared memory.  The last CTA to run out of units resets the
+// counters for the next launch.
 // ---------------------------------------------------------------------------
-constexpr int kBsr2Threads = 256;            // 2 warp groups x 128 threads, 2 columns each
-constexpr int kBsr2Cols = kBsr2Threads;      // columns of A (rows of W) per CTA
-constexpr int kBsr2PerWg = kBsrGroupF32 / 2; // atoms per warp group
+constexpr int kBsrPThreads = 128;
+constexpr int kBsrStages = 6;
 
-__device__ __forceinline__ void cmac2(float& xr, float& xi, float br, float bi, float ar, float ai) {
-  xr = fmaf(br, ar, xr);
-  xr = fmaf(-bi, ai, xr);
-  xi = fmaf(br, ai, xi);
-  xi = fmaf(bi, ar, xi);
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-__global__ void __launch_bounds__(kBsr2Threads, 2) k_bsr_f32x2(const BsrItem* __restrict__ items,
-                                                               const BsrSys* __restrict__ sysv) {
+__global__ void __launch_bounds__(kBsrPThreads, 3) k_bsr_f32p(const BsrItem* __restrict__ items,
+                                                             const BsrSys* __restrict__ sysv,
+                                                             const int* __restrict__ item_u0, int n_items,
+                                                             int* __restrict__ ctr, int max_tg) {
   extern __shared__ __align__(16) unsigned char bsr_smem[];
-  float4* sR = reinterpret_cast<float4*>(bsr_smem);  // block (J, K) = 8 float4: row c = sR[8 s + 2c], [8 s + 2c + 1]
+  float4* sR = reinterpret_cast<float4*>(bsr_smem);                  // [max_tg][8] float4
+  float2* sA = reinterpret_cast<float2*>(bsr_smem + (long long)max_tg * 128);  // [kBsrStages][4][kBsrPThreads]
+  __shared__ int s_unit;
   pdl_wait();
   pdl_trigger();
-  const BsrItem& it = items[blockIdx.y];
-  const BsrSys& S = sysv[it.sys];
-  const int Np = S.Np;
-  const int nch = (Np + kBsr2Cols - 1) / kBsr2Cols;
-  const int u = blockIdx.x;
-  if (u >= S.n_grp * nch) return;
-  const int g = u / nch, ch = u - g * nch;
-  const int wg = threadIdx.x >> 7, tl = threadIdx.x & 127;
-  const int i0 = ch * kBsr2Cols + 2 * tl;  // this thread's rows of W: i0, i0 + 1
-  // Np is a multiple of 128, so in the last chunk of an Np that is not a multiple
-  // of 256 whole warps (64 threads of each warp group) fall outside the matrix
-  const bool live = i0 < Np;
-  const int t0 = S.grp_t0[g], nt = S.grp_t0[g + 1] - t0;
-  const int e0 = S.grp_e0[g], e1 = S.grp_e0[g + 1];
-  // acc[j][c]: W rows i0 (x, y) and i0 + 1 (z, w) in (re, im) pairs
-  float4 acc[kBsr2PerWg][4];
-#pragma unroll
-  for (int j = 0; j < kBsr2PerWg; ++j)
-#pragma unroll
-    for (int c = 0; c < 4; ++c) acc[j][c] = make_float4(0.f, 0.f, 0.f, 0.f);
-
-  for (int sg = 0; sg < it.nseg; ++sg) {
-    const float4* R = reinterpret_cast<const float4*>(reinterpret_cast<const float2*>(it.R[sg]) + 16LL * t0);
+  const int tid = threadIdx.x;
+  const int total = item_u0[n_items];
+  const uint32_t sA_u32 = (uint32_t)__cvta_generic_to_shared(sA);
+  for (;;) {
+    __syncthreads();  // the previous unit's readers of sR are done
+    if (tid == 0) s_unit = atomicAdd(ctr, 1);
     __syncthreads();
-    for (int x = threadIdx.x; x < 8 * nt; x += kBsr2Threads) sR[x] = R[x];
-    __syncthreads();
-    const float2* A = reinterpret_cast<const float2*>(it.A[sg]) + i0;
-    auto load = [&](int e, float4 (&a)[4]) {
-      const float2* p = A + (long long)(4 * __ldg(S.ent_K + e)) * Np;
-#pragma unroll
-      for (int r = 0; r < 4; ++r)
-        a[r] = live ? *reinterpret_cast<const float4*>(p + (long long)r * Np) : make_float4(0.f, 0.f, 0.f, 0.f);
+    const int uu = s_unit;
+    if (uu >= total) break;
+    int itx = 0;
+    while (itx + 1 < n_items && item_u0[itx + 1] <= uu) ++itx;
+    const BsrItem& it = items[itx];
+    const BsrSys& S = sysv[it.sys];
+    const int Np = S.Np;
+    const int nch = Np / kBsrPThreads;
+    const int u = uu - item_u0[itx];
+    const int g = u / nch, ch = u - g * nch;
+    const int i = ch * kBsrPThreads + tid;
+    const int t0 = S.grp_t0[g], nt = S.grp_t0[g + 1] - t0;
+    const int e0 = S.grp_e0[g], ne = S.grp_e0[g + 1] - e0;
+    auto stage_r = [&](int sg) {
+      const float4* R = reinterpret_cast<const float4*>(reinterpret_cast<const float2*>(it.R[sg]) + 16LL * t0);
+      for (int x = tid; x < 8 * nt; x += kBsrPThreads) sR[x] = R[x];
     };
-    float4 a0[4], a1[4];
-    if (e0 < e1) load(e0, a0);
-    for (int e = e0; e < e1; ++e) {
-      if (e + 1 < e1) load(e + 1, a1);
-      // this warp group's members 4 wg .. 4 wg + 3: four shorts of the entry's eight
-      const int2 sw = __ldg(reinterpret_cast<const int2*>(S.ent_slot + (long long)kBsrGroupF32 * e) + wg);
+    stage_r(0);
+    __syncthreads();
+    const int nsteps = it.nseg * ne;  // entries of segment 0, then of segment 1
+    auto issue = [&](int st) {
+      if (st < nsteps) {
+        const int sg = st >= ne ? 1 : 0;
+        const int e = e0 + st - sg * ne;
+        const float2* p = reinterpret_cast<const float2*>(it.A[sg]) + (long long)(4 * __ldg(S.ent_K + e)) * Np + i;
+        const uint32_t d = sA_u32 + (uint32_t)(((st % kBsrStages) * 4 * kBsrPThreads + tid) * 8);
 #pragma unroll
-      for (int j = 0; j < kBsr2PerWg; ++j) {
-        const int word = (j < 2) ? sw.x : sw.y;
-        const int s = (int)(short)((uint32_t)word >> (16 * (j & 1)));
+        for (int r = 0; r < 4; ++r) cp_async8(d + r * kBsrPThreads * 8, p + (long long)r * Np);
+      }
+      cp_async_commit();
+    };
+#pragma unroll
+    for (int st = 0; st < kBsrStages - 1; ++st) issue(st);
+    float ar[kBsrGroupF32][4], ai[kBsrGroupF32][4];
+#pragma unroll
+    for (int j = 0; j < kBsrGroupF32; ++j)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) ar[j][c] = ai[j][c] = 0.f;
+    for (int st = 0; st < nsteps; ++st) {
+      if (st == ne) {  // segment 1 begins: its R blocks replace segment 0's
+        __syncthreads();
+        stage_r(1);
+        __syncthreads();
+      }
+      issue(st + kBsrStages - 1);
+      cp_async_wait<kBsrStages - 1>();
+      const int sg = st >= ne ? 1 : 0;
+      const int e = e0 + st - sg * ne;
+      const float2* a_s = sA + (st % kBsrStages) * 4 * kBsrPThreads + tid;
+      const float2 a0 = a_s[0], a1 = a_s[kBsrPThreads], a2 = a_s[2 * kBsrPThreads], a3 = a_s[3 * kBsrPThreads];
+      const Slots<kBsrGroupF32> sl = load_slots<kBsrGroupF32>(S.ent_slot + (long long)kBsrGroupF32 * e);
+      const float4* Rs = sR;
+#pragma unroll
+      for (int j = 0; j < kBsrGroupF32; ++j) {
+        const int s = sl.get(j);
         if (s >= 0) {
-          const float4* b = sR + 8 * s;
+          const float4* b = Rs + 8 * s;
 #pragma unroll
           for (int c = 0; c < 4; ++c) {
             const float4 b01 = b[2 * c], b23 = b[2 * c + 1];  // R_JK[c][0..3] as (re, im) pairs
-            float4& x = acc[j][c];
-            cmac2(x.x, x.y, b01.x, b01.y, a0[0].x, a0[0].y);
-            cmac2(x.z, x.w, b01.x, b01.y, a0[0].z, a0[0].w);
-            cmac2(x.x, x.y, b01.z, b01.w, a0[1].x, a0[1].y);
-            cmac2(x.z, x.w, b01.z, b01.w, a0[1].z, a0[1].w);
-            cmac2(x.x, x.y, b23.x, b23.y, a0[2].x, a0[2].y);
-            cmac2(x.z, x.w, b23.x, b23.y, a0[2].z, a0[2].w);
-            cmac2(x.x, x.y, b23.z, b23.w, a0[3].x, a0[3].y);
-            cmac2(x.z, x.w, b23.z, b23.w, a0[3].z, a0[3].w);
+            float xr = ar[j][c], xi = ai[j][c];
+            xr = fmaf(b01.x, a0.x, xr); xr = fmaf(-b01.y, a0.y, xr); xi = fmaf(b01.x, a0.y, xi); xi = fmaf(b01.y, a0.x, xi);
+            xr = fmaf(b01.z, a1.x, xr); xr = fmaf(-b01.w, a1.y, xr); xi = fmaf(b01.z, a1.y, xi); xi = fmaf(b01.w, a1.x, xi);
+            xr = fmaf(b23.x, a2.x, xr); xr = fmaf(-b23.y, a2.y, xr); xi = fmaf(b23.x, a2.y, xi); xi = fmaf(b23.y, a2.x, xi);
+            xr = fmaf(b23.z, a3.x, xr); xr = fmaf(-b23.w, a3.y, xr); xi = fmaf(b23.z, a3.y, xi); xi = fmaf(b23.w, a3.x, xi);
+            ar[j][c] = xr;
+            ai[j][c] = xi;
           }
         }
       }
-#pragma unroll
-      for (int r = 0; r < 4; ++r) a0[r] = a1[r];
     }
-  }
-
-  // W[i, 4J + c] = conj(acc) for J = 8 g + 4 wg + j < nat, rows i0 and i0 + 1,
-  // as embedded BF16 pieces (row stride 2 Np; hi at 0, lo at 4 Np^2):
-  // top row i = [Wr | Wi], bottom row Np + i = [-Wi | Wr]
-  const int J0 = kBsrGroupF32 * g + kBsr2PerWg * wg;
-  const int cnt = live ? min(kBsr2PerWg, S.nat - J0) : 0;
-  __nv_bfloat16* P = reinterpret_cast<__nv_bfloat16*>(it.W);
-  const long long P1 = 4LL * Np * Np, ld = 2LL * Np;
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int i = i0 + h;
+    cp_async_wait<0>();
+    // W[i, 4J + c] = conj(acc) as embedded BF16 pieces (row stride 2 Np; hi at 0,
+    // lo at 4 Np^2): top row i = [Wr | Wi], bottom row Np + i = [-Wi | Wr]
+    const int J0 = kBsrGroupF32 * g;
+    const int cnt = min(kBsrGroupF32, S.nat - J0);
+    __nv_bfloat16* P = reinterpret_cast<__nv_bfloat16*>(it.W);
+    const long long P1 = 4LL * Np * Np, ld = 2LL * Np;
     const long long top = (long long)i * ld + 4 * J0, bot = (long long)(Np + i) * ld + 4 * J0;
 #pragma unroll
-    for (int j = 0; j < kBsr2PerWg; ++j) {
+    for (int j = 0; j < kBsrGroupF32; ++j) {
       if (j < cnt) {
         float wr[4], wi[4], nwi[4];
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-          const float xr = h ? acc[j][c].z : acc[j][c].x, xi = h ? acc[j][c].w : acc[j][c].y;
-          wr[c] = xr;
-          wi[c] = -xi;
-          nwi[c] = xi;
+          wr[c] = ar[j][c];
+          wi[c] = -ai[j][c];
+          nwi[c] = ai[j][c];
         }
         uint2 rh, rl, ih, il, nh, nl;
         split4(wr, rh, rl);
@@ -332,6 +352,19 @@ __global__ void __launch_bounds__(kBsr2Threads, 2) k_bsr_f32x2(const BsrItem* __
       }
     }
   }
+  // the last CTA out resets the unit counter for the next launch
+  if (tid == 0) {
+    __threadfence();
+    if (atomicAdd(ctr + 1, 1) == (int)gridDim.x - 1) {
+      ctr[0] = 0;
+      ctr[1] = 0;
+      __threadfence();
+    }
+  }
+}
+
+size_t bsr_p_smem_bytes(int max_grp_targets) {
+  return (size_t)max_grp_targets * 128 + (size_t)kBsrStages * 4 * kBsrPThreads * sizeof(float2);
 }
 
 int bsr_group(int fp64) { return fp64 ? kBsrGroupF64 : kBsrGroupF32; }
@@ -341,26 +374,32 @@ size_t bsr_smem_bytes(int fp64, int max_grp_targets) {
 }
 
 int bsr_configure(int fp64, int max_grp_targets) {
-  const size_t smem = bsr_smem_bytes(fp64, max_grp_targets);
+  const size_t smem = fp64 ? bsr_smem_bytes(1, max_grp_targets) : bsr_p_smem_bytes(max_grp_targets);
   if (smem > 227 * 1024) return -1;
   cudaError_t e = fp64 ? cudaFuncSetAttribute(k_bsr<double, kBsrGroupF64>,
                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-                       : cudaFuncSetAttribute(k_bsr_f32x2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                       : cudaFuncSetAttribute(k_bsr_f32p, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   return e == cudaSuccess ? 0 : -1;
 }
 
 int bsr_units(int fp64, int n_grp, int Np) {
-  return n_grp * (fp64 ? Np / kBsrThreads : (Np + kBsr2Cols - 1) / kBsr2Cols);
+  (void)fp64;  // both kernels take 128 columns of A per unit
+  return n_grp * (Np / 128);
 }
 
-void launch_bsr(const BsrItem* items, const BsrSys* sys, int n_items, int max_units, int fp64, int max_grp_targets,
-                const int* step, cudaStream_t st) {
-  const dim3 grid(max_units, n_items);
-  const size_t smem = bsr_smem_bytes(fp64, max_grp_targets);
-  if (fp64)
-    launch_pdl(k_bsr<double, kBsrGroupF64>, grid, kBsrThreads, smem, st, items, sys, step);
-  else
-    launch_pdl(k_bsr_f32x2, grid, kBsr2Threads, smem, st, items, sys);
+void launch_bsr(const BsrItem* items, const BsrSys* sys, int n_items, int max_units, int total_units,
+                const int* item_u0, int* ctr, int fp64, int max_grp_targets, const int* step, cudaStream_t st) {
+  if (fp64) {
+    launch_pdl(k_bsr<double, kBsrGroupF64>, dim3(max_units, n_items), kBsrThreads, bsr_smem_bytes(1, max_grp_targets),
+               st, items, sys, step);
+    return;
+  }
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = std::min(total_units, 3 * nsm);  // resident CTAs: 3 per SM (registers, shared memory)
+  launch_pdl(k_bsr_f32p, grid, kBsrPThreads, bsr_p_smem_bytes(max_grp_targets), st, items, sys, item_u0, n_items, ctr,
+             max_grp_targets);
 }
 
 }  // namespace vgtb

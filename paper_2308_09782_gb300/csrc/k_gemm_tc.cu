@@ -135,6 +135,66 @@ int tc_gemm_supported() {
   return (maj == 10 && min == 3) ? 1 : 0;
 }
 
+// Nonzero k-panels of each B column tile of product 1 for system v (tile width
+// bw rows of the embedded [[Re H, Im H], [-Im H, Re H]]): a panel kt covers the
+// 64 columns k' = 64 kt .. 64 kt + 63 of a segment, i.e. H columns k' (real
+// half) or k' - Np (imaginary half); it is nonzero for the tile when some H row
+// of the tile (row n' or n' - Np) belongs to an atom I with a target (I, J) whose
+// columns meet the panel.  H and dH share the pattern.
+// uniform = true pads every tile's list with panels of zeros (in increasing
+// order) to the longest list, so that all tiles take the same number of
+// k-iterations, as the stream-K schedules need.
+static void zero_panel_lists(const TcSysView& v, int bw, bool uniform, std::vector<int>& kofs,
+                             std::vector<short>& kidx) {
+  const std::vector<int>& off = *v.orb_off;
+  const int nat = (int)off.size() - 1, N = off[nat], Np = v.Np;
+  const int npan = 2 * Np / BK;
+  std::vector<int> atom_of(N);
+  for (int a = 0; a < nat; ++a)
+    for (int o = off[a]; o < off[a + 1]; ++o) atom_of[o] = a;
+  std::vector<std::vector<int>> nbr(nat);
+  for (size_t t = 0; t < v.tgt_I->size(); ++t) nbr[(*v.tgt_I)[t]].push_back((*v.tgt_J)[t]);
+  const int tiles_n = 2 * Np / bw;
+  std::vector<std::vector<char>> pans(tiles_n);
+  size_t longest = 1;
+  for (int nt = 0; nt < tiles_n; ++nt) {
+    std::vector<char> atoms(nat, 0), pan(npan, 0);
+    for (int r = nt * bw; r < (nt + 1) * bw; ++r) {
+      const int row = r < Np ? r : r - Np;
+      if (row < N) atoms[atom_of[row]] = 1;
+    }
+    for (int a = 0; a < nat; ++a)
+      if (atoms[a])
+        for (int J : nbr[a])
+          for (int c = off[J]; c < off[J + 1]; ++c) {
+            pan[c / BK] = 1;
+            pan[(Np + c) / BK] = 1;
+          }
+    size_t cnt = 0;
+    for (int k = 0; k < npan; ++k) cnt += pan[k] ? 1 : 0;
+    longest = std::max(longest, cnt);
+    pans[nt] = pan;
+  }
+  kofs.assign(1, 0);
+  kidx.clear();
+  for (int nt = 0; nt < tiles_n; ++nt) {
+    std::vector<char>& pan = pans[nt];
+    size_t cnt = 0;
+    for (int k = 0; k < npan; ++k) cnt += pan[k] ? 1 : 0;
+    // a tile of padding rows only gets one panel of zeros, which clears its accumulator;
+    // with uniform lists every tile is padded with zero panels to the longest list
+    const size_t want = uniform ? longest : std::max<size_t>(cnt, 1);
+    for (int k = 0; k < npan && cnt < want; ++k)
+      if (!pan[k]) {
+        pan[k] = 2;
+        ++cnt;
+      }
+    for (int k = 0; k < npan; ++k)
+      if (pan[k]) kidx.push_back((short)k);
+    kofs.push_back(kofs.back() + (int)cnt);
+  }
+}
+
 static int build_one(const std::vector<TcSysView>& sys, const std::vector<DevItem>& items, int epi, int variant,
                      long long timeout_ns, TcPlan* plan, std::string* msg) {
   const int BNv = kVariants[variant].bn;
@@ -161,8 +221,37 @@ static int build_one(const std::vector<TcSysView>& sys, const std::vector<DevIte
       if (!encode_map(&plan->P.mB[s][0], v.Wemb_p, 2 * Np, 2 * Np, v.n_items, bbox, msg)) return -1;
     }
   }
+  // zero-panel skipping: product 1, every system's pattern known; the stream-K
+  // schedules get lists of one length per system (see zero_panel_lists)
+  bool skip = epi == 0;
+  const bool uniform = kVariants[variant].streamk != 0;
+  for (const TcSysView& v : sys) skip = skip && v.orb_off && v.tgt_I && v.tgt_J;
+  std::vector<int> sys_kofs0(sys.size(), 0), sys_kidx0(sys.size(), 0), all_kofs;
+  std::vector<short> all_kidx;
+  std::vector<std::vector<int>> sys_cnt(sys.size());
+  if (skip) {
+    for (size_t s = 0; s < sys.size(); ++s) {
+      std::vector<int> kofs;
+      std::vector<short> kidx;
+      zero_panel_lists(sys[s], BNv, uniform, kofs, kidx);
+      sys_kofs0[s] = (int)all_kofs.size();
+      sys_kidx0[s] = (int)all_kidx.size();
+      for (size_t i = 0; i + 1 < kofs.size(); ++i) sys_cnt[s].push_back(kofs[i + 1] - kofs[i]);
+      all_kofs.insert(all_kofs.end(), kofs.begin(), kofs.end());
+      all_kidx.insert(all_kidx.end(), kidx.begin(), kidx.end());
+    }
+    if (cudaMalloc(&plan->d_kofs, sizeof(int) * all_kofs.size()) != cudaSuccess ||
+        cudaMalloc(&plan->d_kidx, sizeof(short) * all_kidx.size()) != cudaSuccess) {
+      *msg = "cudaMalloc failed for the k-panel lists";
+      return -1;
+    }
+    cudaMemcpy(plan->d_kofs, all_kofs.data(), sizeof(int) * all_kofs.size(), cudaMemcpyHostToDevice);
+    cudaMemcpy(plan->d_kidx, all_kidx.data(), sizeof(short) * all_kidx.size(), cudaMemcpyHostToDevice);
+    plan->skip = true;
+  }
   std::vector<TcProb> probs;
   std::vector<int> local(sys.size(), 0);
+  std::vector<std::pair<int, int>> tile_cost;  // (k-panels, tile) for the longest-first order
   int tiles = 0;
   long long iters = 0;
   for (const DevItem& it : items) {
@@ -184,9 +273,17 @@ static int build_one(const std::vector<TcSysView>& sys, const std::vector<DevIte
       pr.a_b[0] = it.k;
       pr.b_b[0] = li;
       pr.out = it.Xf;
+      pr.addend = v.R0f ? v.R0f + 2LL * v.Np * v.Np * it.k : nullptr;
     }
     pr.kt = (epi == 0 ? 2 : 1) * (2 * v.Np) / BK;
     pr.iter0 = (int)iters;
+    if (skip) {
+      pr.kofs = plan->d_kofs + sys_kofs0[it.sys];
+      pr.kidx = plan->d_kidx + sys_kidx0[it.sys];
+      pr.kt = 2 * sys_cnt[it.sys][0];  // every segment takes the panel list (uniform lists: one length)
+      for (int nt = 0; nt < pr.tiles_n; ++nt)
+        for (int mt = 0; mt < pr.tiles_m; ++mt) tile_cost.push_back({sys_cnt[it.sys][nt], tiles + nt * pr.tiles_m + mt});
+    }
     tiles += pr.tiles_m * pr.tiles_n;
     iters += (long long)pr.tiles_m * pr.tiles_n * pr.kt;
     probs.push_back(pr);
@@ -201,6 +298,19 @@ static int build_one(const std::vector<TcSysView>& sys, const std::vector<DevIte
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (skip && !uniform) {
+    // tiles of unequal length: the workers take them longest first
+    std::stable_sort(tile_cost.begin(), tile_cost.end(),
+                     [](const std::pair<int, int>& a, const std::pair<int, int>& b) { return a.first > b.first; });
+    std::vector<int> tord(tile_cost.size());
+    for (size_t i = 0; i < tord.size(); ++i) tord[i] = tile_cost[i].second;
+    if (cudaMalloc(&plan->d_tord, sizeof(int) * tord.size()) != cudaSuccess) {
+      *msg = "cudaMalloc failed for the tile order";
+      return -1;
+    }
+    cudaMemcpy(plan->d_tord, tord.data(), sizeof(int) * tord.size(), cudaMemcpyHostToDevice);
+    plan->P.tord = plan->d_tord;
+  }
   plan->P.probs = plan->d_probs;
   plan->P.n_prob = (int)probs.size();
   plan->P.total_tiles = tiles;
@@ -352,9 +462,18 @@ void tc_destroy_plan(TcPlan* p) {
   if (p->d_err) cudaFree(p->d_err);
   if (p->d_ws) cudaFree(p->d_ws);
   if (p->d_flags) cudaFree(p->d_flags);
+  if (p->d_kofs) cudaFree(p->d_kofs);
+  if (p->d_kidx) cudaFree(p->d_kidx);
+  if (p->d_tord) cudaFree(p->d_tord);
   delete p;
 }
 
 int tc_plan_variant(const TcPlan* p) { return p ? p->variant : -1; }
+
+int tc_plan_info(const TcPlan* p, int* out4) {
+  if (!p || tc_variant_info(p->variant, out4)) return -1;
+  if (p->skip) out4[2] += 4;  // 4, 5, 6: the schedule with zero k-panels skipped
+  return 0;
+}
 
 }  // namespace vgtb

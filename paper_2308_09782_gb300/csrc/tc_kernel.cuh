@@ -38,6 +38,15 @@ struct TcProb {
   void* out;
   int kt;              // k-iterations per tile (stream-K schedule)
   int iter0;           // first global k-iteration of the problem (stream-K schedule)
+  // classic schedule with zero panels skipped (null = every panel): the
+  // 64-wide k-panels of one segment in which the B rows of column tile nt have
+  // a nonzero are kidx[kofs[nt] .. kofs[nt+1]-1]; every segment uses the list
+  const int* kofs;
+  const short* kidx;
+  // product 2 (FP32 planar output) only, may be null: X += (i/2) addend, addend in
+  // the same planar layout [Re(row) | Im(row)] (the split form folds R0 into X
+  // this way: -i(X' - X'^dagger) = R0 - i(X - X^dagger) for a Hermitian R0)
+  const float* addend;
 };
 
 struct TcParams {
@@ -47,6 +56,7 @@ struct TcParams {
   int n_prob, total_tiles, nseg;
   int* err;
   long long timeout_ns;
+  const int* tord;     // classic schedule: order in which the workers take the tiles (null = 0, 1, ...)
   // stream-K schedule (streamk != 0): the tiles below sk_tile0 (whole waves)
   // go to the workers in turn, as in the classic schedule, so that workers on
   // the same operand rows stay at the same k and share them through L2; worker c
@@ -68,7 +78,11 @@ struct TcPlan {
   int* d_err = nullptr;
   float* d_ws = nullptr;
   int* d_flags = nullptr;
+  int* d_kofs = nullptr;    // zero-panel skipping: panel lists of every system, and the tile order
+  short* d_kidx = nullptr;
+  int* d_tord = nullptr;
   int grid = 0, smem = 0, variant = 0, epi = 0;
+  bool skip = false;
 };
 
 // ----------------------------------------------------------------------------
@@ -184,6 +198,37 @@ __device__ __forceinline__ int find_prob(const TcProb* probs, int n, int t, int 
   return p;
 }
 
+// the problem that owns tile t, by bisection (tiles taken in any order)
+__device__ __forceinline__ int find_prob_any(const TcProb* probs, int n, int t) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (probs[mid].tile0 <= t) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// k-iterations of tile t of problem pr (classic schedule)
+__device__ __forceinline__ int tile_kt(const TcParams& P, const TcProb& pr, int t) {
+  if (!pr.kofs) return P.nseg * (2 * pr.Np) / BK;
+  const int nt = (t - pr.tile0) / pr.tiles_m;
+  return P.nseg * (pr.kofs[nt + 1] - pr.kofs[nt]);
+}
+
+// segment and k-panel of k-iteration kk of tile t
+__device__ __forceinline__ void tile_panel(const TcProb& pr, int t, int kk, int& sg, int& kt) {
+  if (!pr.kofs) {
+    const int kts = (2 * pr.Np) / BK;
+    sg = kk / kts;
+    kt = kk - sg * kts;
+    return;
+  }
+  const int nt = (t - pr.tile0) / pr.tiles_m;
+  const int k0 = pr.kofs[nt], cnt = pr.kofs[nt + 1] - k0;
+  sg = kk / cnt;
+  kt = pr.kidx[k0 + kk - sg * cnt];
+}
+
 // Work units: classic mode walks whole tiles t = blockIdx.x + i G; stream-K
 // mode walks this CTA's k-iteration range, split at tile boundaries.  Every
 // role of the CTA runs the same cursor, so they agree on the sequence.
@@ -209,10 +254,10 @@ __device__ __forceinline__ bool cursor_next(const TcParams& P, UnitCursor& u, in
                                             int& KT) {
   const int t_classic = P.streamk ? P.sk_tile0 : P.total_tiles;
   if (u.t_next < t_classic) {
-    t = u.t_next;
+    t = P.tord ? P.tord[u.t_next] : u.t_next;
     u.t_next += G;
-    u.p = find_prob(P.probs, P.n_prob, t, u.p);
-    KT = P.nseg * (2 * P.probs[u.p].Np) / BK;
+    u.p = P.tord ? find_prob_any(P.probs, P.n_prob, t) : find_prob(P.probs, P.n_prob, t, u.p);
+    KT = tile_kt(P, P.probs[u.p], t);
     kb = 0;
     ke = KT;
     return true;
@@ -322,9 +367,9 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcPa
         const TcProb& pr = P.probs[cur.p];
         const int local = t - pr.tile0;
         const int mt = local % pr.tiles_m, nt = local / pr.tiles_m;
-        const int kts = (2 * pr.Np) / BK;
         for (int kk = kb; kk < ke; ++kk, ++it) {
-          const int sg = kk / kts, kt = kk - sg * kts;
+          int sg, kt;
+          tile_panel(pr, t, kk, sg, kt);
           const CUtensorMap* ma = &P.mA[pr.sys][sg];
           const CUtensorMap* mb = &P.mB[pr.sys][sg];
           const int s = it % ST, r = it / ST;
@@ -452,6 +497,21 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcPa
         const int gn = nt * BN + c0;
         if (EPI == 1) {
           float* X = reinterpret_cast<float*>(pr.out) + row * ld + gn;
+          if (pr.addend) {
+            // (i/2)(a + ib) = -b/2 + i a/2: the real half takes -1/2 of the addend's
+            // imaginary half at the same column, the imaginary half +1/2 of its real half
+            const bool im = gn >= Np;
+            const float h = im ? 0.5f : -0.5f;
+            const float4* ad = reinterpret_cast<const float4*>(pr.addend + row * ld + (im ? gn - Np : gn + Np));
+#pragma unroll
+            for (int v = 0; v < 8; ++v) {
+              const float4 f = __ldg(ad + v);
+              r[4 * v] = __float_as_uint(fmaf(h, f.x, __uint_as_float(r[4 * v])));
+              r[4 * v + 1] = __float_as_uint(fmaf(h, f.y, __uint_as_float(r[4 * v + 1])));
+              r[4 * v + 2] = __float_as_uint(fmaf(h, f.z, __uint_as_float(r[4 * v + 2])));
+              r[4 * v + 3] = __float_as_uint(fmaf(h, f.w, __uint_as_float(r[4 * v + 3])));
+            }
+          }
 #pragma unroll
           for (int v = 0; v < 8; ++v)
             reinterpret_cast<float4*>(X)[v] =
@@ -629,10 +689,10 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm2(const __grid_constant__ TcP
         const TcProb& pr = P.probs[cur.p];
         const int local = t - pr.tile0;
         const int mt = local % pr.tiles_m, nt = local / pr.tiles_m;
-        const int kts = (2 * pr.Np) / BK;
         const int arow = mt * (2 * BM) + rank * BM, brow = nt * BNP + rank * (BNP / 2);
         for (int kk = kb; kk < ke; ++kk, ++it) {
-          const int sg = kk / kts, kt = kk - sg * kts;
+          int sg, kt;
+          tile_panel(pr, t, kk, sg, kt);
           const CUtensorMap* ma = &P.mA[pr.sys][sg];
           const CUtensorMap* mb = &P.mB[pr.sys][sg];
           const int s = it % ST, r = it / ST;
@@ -769,6 +829,21 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm2(const __grid_constant__ TcP
         if (row >= Np) continue;  // last row tile of an Np that is not a multiple of 256
         if (EPI == 1) {
           float* X = reinterpret_cast<float*>(pr.out) + row * ld + gn;
+          if (pr.addend) {
+            // (i/2)(a + ib) = -b/2 + i a/2: the real half takes -1/2 of the addend's
+            // imaginary half at the same column, the imaginary half +1/2 of its real half
+            const bool im = gn >= Np;
+            const float h = im ? 0.5f : -0.5f;
+            const float4* ad = reinterpret_cast<const float4*>(pr.addend + row * ld + (im ? gn - Np : gn + Np));
+#pragma unroll
+            for (int v = 0; v < 8; ++v) {
+              const float4 f = __ldg(ad + v);
+              r[4 * v] = __float_as_uint(fmaf(h, f.x, __uint_as_float(r[4 * v])));
+              r[4 * v + 1] = __float_as_uint(fmaf(h, f.y, __uint_as_float(r[4 * v + 1])));
+              r[4 * v + 2] = __float_as_uint(fmaf(h, f.z, __uint_as_float(r[4 * v + 2])));
+              r[4 * v + 3] = __float_as_uint(fmaf(h, f.w, __uint_as_float(r[4 * v + 3])));
+            }
+          }
 #pragma unroll
           for (int v = 0; v < 8; ++v)
             reinterpret_cast<float4*>(X)[v] =

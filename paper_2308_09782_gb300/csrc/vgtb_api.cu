@@ -119,7 +119,9 @@ struct vgtb_ctx {
   bool bsr = false;
   BsrItem* d_bsr = nullptr;
   BsrSys* d_bsrsys = nullptr;
-  int bsr_units_max = 0, bsr_tg_max = 0;
+  int* d_bsr_u0 = nullptr;   // [n_items+1] first unit of each item
+  int* d_bsr_ctr = nullptr;  // [2] unit counter and finished-CTA counter
+  int bsr_units_max = 0, bsr_units_total = 0, bsr_tg_max = 0;
   // graph
   cudaGraphExec_t graph = nullptr;
   int graph_steps = 0;
@@ -990,8 +992,8 @@ int enqueue_step(vgtb_ctx* ctx, cudaEvent_t* ev) {
                  ctx->delta ? PH_FP64_DELTA : PH_FP64_PLAIN, -1, st);
   if (ev) CK(cudaEventRecordWithFlags(ev[3], st, evflag));
   if (ctx->bsr)
-    launch_bsr(ctx->d_bsr, ctx->d_bsrsys, ctx->n_items, ctx->bsr_units_max, ctx->split ? 0 : 1, ctx->bsr_tg_max,
-               ctx->d_step, st);
+    launch_bsr(ctx->d_bsr, ctx->d_bsrsys, ctx->n_items, ctx->bsr_units_max, ctx->bsr_units_total, ctx->d_bsr_u0,
+               ctx->d_bsr_ctr, ctx->split ? 0 : 1, ctx->bsr_tg_max, ctx->d_step, st);
   if (ctx->split) {
     if (!ctx->bsr)
       TRY(tc_launch(ctx->tc1, st) == 0 ? VGTB_OK : fail(ctx, VGTB_E_CUDA, "tcgen05 product 1 launch failed"));
@@ -1342,7 +1344,7 @@ int vgtb_create_batch(vgtb_ctx** out, int n_sys, const vgtb_system* sys, int n_t
     LeapItem l{};
     l.X = ctx->split ? (const void*)it.Xf : (const void*)it.X;
     l.R0 = (ctx->delta && !ctx->split) ? h.R0 + it.k * NN : nullptr;
-    l.R0f = ctx->split ? h.R0f + 2 * NN * it.k : nullptr;
+    l.R0f = nullptr;  // split form: R0 is added to X by product 2 (k_tc_gemm epilogue)
     l.D[0] = it.D[0];
     l.D[1] = it.D[1];
     l.pieces = it.dD_p;
@@ -1382,6 +1384,11 @@ int vgtb_create_batch(vgtb_ctx** out, int n_sys, const vgtb_system* sys, int n_t
       bl[i] = b;
     }
     if ((rc = upload(ctx, &ctx->d_bsr, bl.data(), bl.size()))) return bail(rc);
+    std::vector<int> u0(ctx->n_items + 1, 0);
+    for (int i = 0; i < ctx->n_items; ++i) u0[i + 1] = u0[i] + ctx->sys[ctx->items_h[i].sys].bsr_units;
+    ctx->bsr_units_total = u0[ctx->n_items];
+    if ((rc = upload(ctx, &ctx->d_bsr_u0, u0.data(), u0.size()))) return bail(rc);
+    if ((rc = dalloc(ctx, &ctx->d_bsr_ctr, 2))) return bail(rc);
   }
   // setup: S^-1, ground state
   for (int s = 0; s < n_sys; ++s) {
@@ -1399,6 +1406,12 @@ int vgtb_create_batch(vgtb_ctx** out, int n_sys, const vgtb_system* sys, int n_t
       views[s].Hemb_p = fam[s].Hemb;
       views[s].dHemb_p = fam[s].dHemb;
       views[s].Wemb_p = fam[s].Wemb;
+      views[s].R0f = ctx->sys[s].R0f;  // R0 joins X in product 2's epilogue
+      if (ctx->opt.product1 != VGTB_P1_DENSE) {  // nonzero pattern: zero k-panels of product 1 are skipped
+        views[s].orb_off = &ctx->sys[s].orb_off;
+        views[s].tgt_I = &ctx->sys[s].tgt_I;
+        views[s].tgt_J = &ctx->sys[s].tgt_J;
+      }
     }
     std::string msg;
     if (tc_build_plans(views, ctx->items_h, ctx->opt.timeout_ns, ctx->opt.autotune, ctx->opt.tile_variant, ctx->stream,
@@ -1790,7 +1803,7 @@ int vgtb_tile_config(const vgtb_ctx* ctx, int product, int* cfg) {
     cfg[3] = 0;
     return VGTB_OK;
   }
-  return tc_variant_info(tc_plan_variant(product == 1 ? ctx->tc1 : ctx->tc2), cfg) == 0 ? VGTB_OK : VGTB_E_STATE;
+  return tc_plan_info(product == 1 ? ctx->tc1 : ctx->tc2, cfg) == 0 ? VGTB_OK : VGTB_E_STATE;
 }
 
 const char* vgtb_last_error(const vgtb_ctx* ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }

@@ -212,8 +212,11 @@ int bsr_group(int fp64);
 size_t bsr_smem_bytes(int fp64, int max_grp_targets);
 int bsr_configure(int fp64, int max_grp_targets);
 int bsr_units(int fp64, int n_grp, int Np);  // CTAs per item
-void launch_bsr(const BsrItem* items, const BsrSys* sys, int n_items, int max_units, int fp64, int max_grp_targets,
-                const int* step, cudaStream_t st);
+// FP64: grid (max_units, n_items); split form: persistent CTAs taking units
+// 0..total_units-1 (item it owns item_u0[it] .. item_u0[it+1]-1) from the
+// counter pair ctr[2] (zero before the first launch; reset by each launch)
+void launch_bsr(const BsrItem* items, const BsrSys* sys, int n_items, int max_units, int total_units,
+                const int* item_u0, int* ctr, int fp64, int max_grp_targets, const int* step, cudaStream_t st);
 
 // Crank-Nicolson convergence check of one item: max |Y[a] - Y[b]| over nocc x N
 struct CnCheckItem {

@@ -106,6 +106,11 @@ __global__ void k_na_prob(TcProb* prob, int* err, int Np, float* out) {
   p.tile0 = 0;
   p.Np = Np;
   p.out = out;
+  p.kt = 0;
+  p.iter0 = 0;
+  p.kofs = nullptr;  // every k-panel
+  p.kidx = nullptr;
+  p.addend = nullptr;
   *prob = p;
   *err = 0;
 }

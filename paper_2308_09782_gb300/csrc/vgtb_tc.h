@@ -19,6 +19,16 @@ struct TcSysView {
   __nv_bfloat16* Hemb_p;   // [n_items][2][2Np][2Np]
   __nv_bfloat16* dHemb_p;  // [n_items][2][2Np][2Np]
   __nv_bfloat16* Wemb_p;   // [n_items][2][2Np][2Np]
+  // nonzero pattern of H_k (host data, may be null): orbital offsets of the
+  // atoms and the atom pairs (I, J) of the targets.  With it, the classic
+  // schedules of product 1 skip the k-panels in which a tile's rows of H and dH
+  // are zero.
+  // product 2: if set, X += (i/2) R0 in its epilogue ([nk][Np][2Np] planar FP32,
+  // Hermitian), so that the leapfrog reads no R0
+  const float* R0f = nullptr;
+  const std::vector<int>* orb_off = nullptr;
+  const std::vector<int>* tgt_I = nullptr;
+  const std::vector<int>* tgt_J = nullptr;
 };
 
 // Plans for the two products of the split form, over every item:
@@ -34,6 +44,8 @@ int tc_build_plans(const std::vector<TcSysView>& sys, const std::vector<DevItem>
 int tc_num_variants();
 // {tile width, pipeline stages, schedule (0 classic, 1 stream-K, 2 classic waves + stream-K rest), 2-SM pair}
 int tc_variant_info(int v, int* out4);
+// tc_variant_info of the plan, with schedule 4 for a classic schedule that skips zero k-panels
+int tc_plan_info(const TcPlan* p, int* out4);
 int tc_launch(TcPlan* p, cudaStream_t st);
 int tc_status(TcPlan* p, cudaStream_t st);  // 0 or the plan's device error word
 void tc_destroy_plan(TcPlan* p);

@@ -337,7 +337,9 @@ class Context:
         if cfg[2] == 3:
             return {"schedule": "block-sparse", "atoms_per_group": cfg[0], "rows_per_cta": cfg[1]}
         return {"tile_n": cfg[0], "stages": cfg[1],
-                "schedule": ("classic", "stream-K", "classic waves + stream-K")[cfg[2]], "pair": bool(cfg[3])}
+                "schedule": ("classic", "stream-K", "classic waves + stream-K", "block-sparse",
+                             "classic, zero k-panels skipped", "stream-K, zero k-panels skipped",
+                             "classic waves + stream-K, zero k-panels skipped")[cfg[2]], "pair": bool(cfg[3])}
 
     def kernel_stats(self):
         n = len(KERNEL_CLASSES)

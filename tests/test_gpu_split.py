@@ -113,6 +113,31 @@ def test_split_timeout_returns_error_and_context_recovers():
     assert np.all(np.isfinite(J))
 
 
+@pytest.mark.parametrize("variant", [0, 5, 1])
+def test_zero_panel_skipping_matches_the_dense_product(variant):
+    """Product 1 skips the k-panels in which a tile's rows of H and dH are zero
+    (512 atoms: 48 of 64 panels remain for 256-wide tiles, 36 for 128-wide).
+    Those panels contribute exact zeros, so with a classic schedule (2-SM pair
+    256-wide tiles, variant 0; single-CTA 128-wide tiles, variant 5) the
+    propagation equals the dense product (product1 = DENSE, same variant) bit for
+    bit; with stream-K (variant 1) the k-ranges of the workers move, so the FP32
+    partial sums meet in another order: J within 1e-6.  50 steps."""
+    from paper_2308_09782_gb300 import vgtb
+    name, nsteps = "si512_kick", 50
+    tv = [variant, 0]
+    with gpu_run(name, nsteps, precision=vgtb.SPLIT_BF16X3, tile_variant=tv) as a, \
+            gpu_run(name, nsteps, precision=vgtb.SPLIT_BF16X3, tile_variant=tv, product1=vgtb.P1_DENSE) as b:
+        assert "zero k-panels skipped" in a.tile_config(1)["schedule"]
+        assert "skipped" not in b.tile_config(1)["schedule"]
+        Ja, _, _ = a.observables(0)
+        Jb, _, _ = b.observables(0)
+        if variant == 1:
+            assert rel_fro([Ja], [Jb]) <= 1e-6
+        else:
+            assert np.array_equal(Ja, Jb)
+            assert np.array_equal(a.get_density(0, 0), b.get_density(0, 0))
+
+
 def test_split_rerun_bitwise_and_autotuned_variants_agree():
     """The stream-K fixup sums partials in a fixed order: reruns are bitwise equal.
     The autotuner's choice (stream-K or classic tiles, 128 or 256 wide) stays within
