@@ -265,7 +265,7 @@ def hbm_rates(sysd, Np, kern_ms, peak_gbs, sparse=True):
     nat = len(norb)
     nk = len(sysd["wk"])
     byts = {
-        "leap": 48 * Np * Np,                                        # X f32 (R0 folded in); dD r/w f64; f32 copy or pieces
+        "leap": 56 * Np * Np,                                        # X, R0 f32; dD r/w f64; f32 copy or pieces
         # S, H0, dS f32 per image; out: H and dH at the nonzeros (2 x float2) or embedded BF16 pieces (16 x 2 B)
         "phase": nk * (20 * el_img + 8 * len(blk) + (16 if sparse else 32) * n_el),
         "obs": nk * 96 * n_el + 40 * nat,                            # dD f64 + S, P, H0 blocks f64

@@ -229,10 +229,8 @@ void launch_leap(const LeapItem* items, int n_items, int Np_max, int x_f32, cons
 }
 
 // ---------------------------------------------------------------------------
-// Leapfrog of the split form: X (FP32 planar; the split form's product 2 has
-// already added (i/2) R0 to it, which is exact in the mirror sums below because
-// R0 is Hermitian) and optionally R0 (FP32 planar) give dD/dt in FP32 with the
-// same mirror-exact operations as k_leap; only the
+// Leapfrog of the split form: X (FP32 planar) and R0 (FP32 planar) give
+// dD/dt in FP32 with the same mirror-exact operations as k_leap; only the
 // master update dD_{n+1} = dD_{n-1} + 2 dt dD/dt is FP64 (GB300's FP64 rate is
 // low, so FP64 is kept to the accumulation that needs it).  The operand of the
 // next first product is written from the new level's FP32 rounding: its FP32

@@ -273,7 +273,6 @@ static int build_one(const std::vector<TcSysView>& sys, const std::vector<DevIte
       pr.a_b[0] = it.k;
       pr.b_b[0] = li;
       pr.out = it.Xf;
-      pr.addend = v.R0f ? v.R0f + 2LL * v.Np * v.Np * it.k : nullptr;
     }
     pr.kt = (epi == 0 ? 2 : 1) * (2 * v.Np) / BK;
     pr.iter0 = (int)iters;

@@ -43,10 +43,6 @@ struct TcProb {
   // a nonzero are kidx[kofs[nt] .. kofs[nt+1]-1]; every segment uses the list
   const int* kofs;
   const short* kidx;
-  // product 2 (FP32 planar output) only, may be null: X += (i/2) addend, addend in
-  // the same planar layout [Re(row) | Im(row)] (the split form folds R0 into X
-  // this way: -i(X' - X'^dagger) = R0 - i(X - X^dagger) for a Hermitian R0)
-  const float* addend;
 };
 
 struct TcParams {
@@ -497,21 +493,6 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcPa
         const int gn = nt * BN + c0;
         if (EPI == 1) {
           float* X = reinterpret_cast<float*>(pr.out) + row * ld + gn;
-          if (pr.addend) {
-            // (i/2)(a + ib) = -b/2 + i a/2: the real half takes -1/2 of the addend's
-            // imaginary half at the same column, the imaginary half +1/2 of its real half
-            const bool im = gn >= Np;
-            const float h = im ? 0.5f : -0.5f;
-            const float4* ad = reinterpret_cast<const float4*>(pr.addend + row * ld + (im ? gn - Np : gn + Np));
-#pragma unroll
-            for (int v = 0; v < 8; ++v) {
-              const float4 f = __ldg(ad + v);
-              r[4 * v] = __float_as_uint(fmaf(h, f.x, __uint_as_float(r[4 * v])));
-              r[4 * v + 1] = __float_as_uint(fmaf(h, f.y, __uint_as_float(r[4 * v + 1])));
-              r[4 * v + 2] = __float_as_uint(fmaf(h, f.z, __uint_as_float(r[4 * v + 2])));
-              r[4 * v + 3] = __float_as_uint(fmaf(h, f.w, __uint_as_float(r[4 * v + 3])));
-            }
-          }
 #pragma unroll
           for (int v = 0; v < 8; ++v)
             reinterpret_cast<float4*>(X)[v] =
@@ -829,21 +810,6 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm2(const __grid_constant__ TcP
         if (row >= Np) continue;  // last row tile of an Np that is not a multiple of 256
         if (EPI == 1) {
           float* X = reinterpret_cast<float*>(pr.out) + row * ld + gn;
-          if (pr.addend) {
-            // (i/2)(a + ib) = -b/2 + i a/2: the real half takes -1/2 of the addend's
-            // imaginary half at the same column, the imaginary half +1/2 of its real half
-            const bool im = gn >= Np;
-            const float h = im ? 0.5f : -0.5f;
-            const float4* ad = reinterpret_cast<const float4*>(pr.addend + row * ld + (im ? gn - Np : gn + Np));
-#pragma unroll
-            for (int v = 0; v < 8; ++v) {
-              const float4 f = __ldg(ad + v);
-              r[4 * v] = __float_as_uint(fmaf(h, f.x, __uint_as_float(r[4 * v])));
-              r[4 * v + 1] = __float_as_uint(fmaf(h, f.y, __uint_as_float(r[4 * v + 1])));
-              r[4 * v + 2] = __float_as_uint(fmaf(h, f.z, __uint_as_float(r[4 * v + 2])));
-              r[4 * v + 3] = __float_as_uint(fmaf(h, f.w, __uint_as_float(r[4 * v + 3])));
-            }
-          }
 #pragma unroll
           for (int v = 0; v < 8; ++v)
             reinterpret_cast<float4*>(X)[v] =

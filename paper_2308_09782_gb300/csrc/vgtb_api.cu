@@ -1344,7 +1344,7 @@ int vgtb_create_batch(vgtb_ctx** out, int n_sys, const vgtb_system* sys, int n_t
     LeapItem l{};
     l.X = ctx->split ? (const void*)it.Xf : (const void*)it.X;
     l.R0 = (ctx->delta && !ctx->split) ? h.R0 + it.k * NN : nullptr;
-    l.R0f = nullptr;  // split form: R0 is added to X by product 2 (k_tc_gemm epilogue)
+    l.R0f = ctx->split ? h.R0f + 2 * NN * it.k : nullptr;
     l.D[0] = it.D[0];
     l.D[1] = it.D[1];
     l.pieces = it.dD_p;
@@ -1406,7 +1406,6 @@ int vgtb_create_batch(vgtb_ctx** out, int n_sys, const vgtb_system* sys, int n_t
       views[s].Hemb_p = fam[s].Hemb;
       views[s].dHemb_p = fam[s].dHemb;
       views[s].Wemb_p = fam[s].Wemb;
-      views[s].R0f = ctx->sys[s].R0f;  // R0 joins X in product 2's epilogue
       if (ctx->opt.product1 != VGTB_P1_DENSE) {  // nonzero pattern: zero k-panels of product 1 are skipped
         views[s].orb_off = &ctx->sys[s].orb_off;
         views[s].tgt_I = &ctx->sys[s].tgt_I;

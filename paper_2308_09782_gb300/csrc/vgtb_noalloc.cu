@@ -110,7 +110,6 @@ __global__ void k_na_prob(TcProb* prob, int* err, int Np, float* out) {
   p.iter0 = 0;
   p.kofs = nullptr;  // every k-panel
   p.kidx = nullptr;
-  p.addend = nullptr;
   *prob = p;
   *err = 0;
 }

@@ -23,9 +23,6 @@ struct TcSysView {
   // atoms and the atom pairs (I, J) of the targets.  With it, the classic
   // schedules of product 1 skip the k-panels in which a tile's rows of H and dH
   // are zero.
-  // product 2: if set, X += (i/2) R0 in its epilogue ([nk][Np][2Np] planar FP32,
-  // Hermitian), so that the leapfrog reads no R0
-  const float* R0f = nullptr;
   const std::vector<int>* orb_off = nullptr;
   const std::vector<int>* tgt_I = nullptr;
   const std::vector<int>* tgt_J = nullptr;
