@@ -643,18 +643,22 @@ void launch_phase(const DevSys* sys, const DevTraj* trj, const DevItem* items, c
 // Phase build, split form: the delta-form H and dH summed in FP32 and stored
 // either at the target elements in FP32 (block-sparse first product) or as the
 // embedded real matrix [[Re, Im], [-Im, Re]] in BF16 hi/lo pieces (the B
-// operand of the dense tcgen05 first product).
+// operand of the tcgen05 first product), whose rows the first product takes
+// interleaved in blocks of four: row r of [Re, Im] is stored as row
+// emb_row_re(r) = 8 (r / 4) + r % 4 and row r of [-Im, Re] as emb_row_re(r) + 4.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ long long emb_row_re(int r) { return 8LL * (r >> 2) + (r & 3); }
+
 __device__ __forceinline__ void store_emb_f(__nv_bfloat16* base, int Np, int r, int c, float re, float im) {
   const long long P = 4LL * Np * Np;
   const long long ld = 2LL * Np;
   const __nv_bfloat16 rh = __float2bfloat16_rn(re), ih = __float2bfloat16_rn(im);
   const __nv_bfloat16 rl = __float2bfloat16_rn(re - __bfloat162float(rh));
   const __nv_bfloat16 il = __float2bfloat16_rn(im - __bfloat162float(ih));
-  const long long i00 = (long long)r * ld + c;
-  const long long i01 = (long long)r * ld + Np + c;
-  const long long i10 = (long long)(Np + r) * ld + c;
-  const long long i11 = (long long)(Np + r) * ld + Np + c;
+  const long long i00 = emb_row_re(r) * ld + c;
+  const long long i01 = emb_row_re(r) * ld + Np + c;
+  const long long i10 = (emb_row_re(r) + 4) * ld + c;
+  const long long i11 = (emb_row_re(r) + 4) * ld + Np + c;
   base[i00] = rh;
   base[P + i00] = rl;
   base[i01] = ih;
@@ -683,7 +687,7 @@ __device__ __forceinline__ uint2 pack_bf16x4(const __nv_bfloat16 (&v)[4]) {
 }
 
 // four consecutive columns c..c+3 of row r (c a multiple of 4): one 8-byte store per
-// quadrant of [[Re, Im], [-Im, Re]] and per piece
+// quadrant of [[Re, Im], [-Im, Re]] and per piece (rows interleaved as above)
 __device__ __forceinline__ void store_emb_f4(__nv_bfloat16* base, int Np, int r, int c, const float (&re)[4],
                                              const float (&im)[4]) {
   const long long P = 4LL * Np * Np;
@@ -698,10 +702,10 @@ __device__ __forceinline__ void store_emb_f4(__nv_bfloat16* base, int Np, int r,
     nh[j] = __hneg(ih[j]);
     nl[j] = __hneg(il[j]);
   }
-  const long long i00 = (long long)r * ld + c;
-  const long long i01 = (long long)r * ld + Np + c;
-  const long long i10 = (long long)(Np + r) * ld + c;
-  const long long i11 = (long long)(Np + r) * ld + Np + c;
+  const long long i00 = emb_row_re(r) * ld + c;
+  const long long i01 = emb_row_re(r) * ld + Np + c;
+  const long long i10 = (emb_row_re(r) + 4) * ld + c;
+  const long long i11 = (emb_row_re(r) + 4) * ld + Np + c;
   const uint2 prh = pack_bf16x4(rh), prl = pack_bf16x4(rl);
   *reinterpret_cast<uint2*>(base + i00) = prh;
   *reinterpret_cast<uint2*>(base + P + i00) = prl;

@@ -433,7 +433,9 @@ void launch_split_planar(const double2* src, __nv_bfloat16* dst, int N, int Np, 
   k_split_planar<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(src, dst, Np);
 }
 
-// embedded pieces [[Re, Im], [-Im, Re]] of a dense complex matrix (2Np x 2Np per piece)
+// embedded pieces [[Re, Im], [-Im, Re]] of a dense complex matrix (2Np x 2Np per
+// piece) in the row order of the first product's B operand: row i of [Re, Im] at
+// 8 (i / 4) + i % 4, row i of [-Im, Re] four rows further
 __global__ void k_split_embedded(const double2* src, __nv_bfloat16* dst, int Np) {
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long NN = (long long)Np * Np;
@@ -444,7 +446,8 @@ __global__ void k_split_embedded(const double2* src, __nv_bfloat16* dst, int Np)
   __nv_bfloat16 rh, rl, ih, il;
   split_bf16_d(v.x, rh, rl);
   split_bf16_d(v.y, ih, il);
-  const long long i00 = i * ld + j, i01 = i * ld + Np + j, i10 = (Np + i) * ld + j, i11 = (Np + i) * ld + Np + j;
+  const long long rr = 8LL * (i >> 2) + (i & 3), ri = rr + 4;
+  const long long i00 = rr * ld + j, i01 = rr * ld + Np + j, i10 = ri * ld + j, i11 = ri * ld + Np + j;
   dst[i00] = rh;
   dst[P + i00] = rl;
   dst[i01] = ih;

@@ -136,11 +136,12 @@ int tc_gemm_supported() {
 }
 
 // Nonzero k-panels of each B column tile of product 1 for system v (tile width
-// bw rows of the embedded [[Re H, Im H], [-Im H, Re H]]): a panel kt covers the
-// 64 columns k' = 64 kt .. 64 kt + 63 of a segment, i.e. H columns k' (real
+// bw rows of the embedded [[Re H, Im H], [-Im H, Re H]], rows interleaved in
+// blocks of four: B row n' holds H row 4 (n' / 8) + n' % 4): a panel kt covers
+// the 64 columns k' = 64 kt .. 64 kt + 63 of a segment, i.e. H columns k' (real
 // half) or k' - Np (imaginary half); it is nonzero for the tile when some H row
-// of the tile (row n' or n' - Np) belongs to an atom I with a target (I, J) whose
-// columns meet the panel.  H and dH share the pattern.
+// of the tile belongs to an atom I with a target (I, J) whose columns meet the
+// panel.  H and dH share the pattern.
 // uniform = true pads every tile's list with panels of zeros (in increasing
 // order) to the longest list, so that all tiles take the same number of
 // k-iterations, as the stream-K schedules need.
@@ -160,7 +161,7 @@ static void zero_panel_lists(const TcSysView& v, int bw, bool uniform, std::vect
   for (int nt = 0; nt < tiles_n; ++nt) {
     std::vector<char> atoms(nat, 0), pan(npan, 0);
     for (int r = nt * bw; r < (nt + 1) * bw; ++r) {
-      const int row = r < Np ? r : r - Np;
+      const int row = 4 * (r / 8) + (r % 4);
       if (row < N) atoms[atom_of[row]] = 1;
     }
     for (int a = 0; a < nat; ++a)

@@ -6,6 +6,12 @@
 //   Aop row m  = [Re A(m,:) | Im A(m,:)]                          ("planar", Np x 2Np)
 //   Bop rows   = [[Re R, Im R], [-Im R, Re R]]                      ("embedded", 2Np x 2Np)
 //   out row m  = [Re C(m,:) | Im C(m,:)].
+// Product 1 (EPI 0) takes its B operand with the rows interleaved in blocks of
+// four: B row 8b + q is row 4b + q of [Re R, Im R] for q < 4 and row 4b + q - 4
+// of [-Im R, Re R] for q >= 4, so a 256-row tile holds the real and imaginary
+// rows of 128 rows of R (32 atoms of an sp3 basis) and meets fewer nonzero
+// k-panels of the block-sparse H; its output column 8b + q is then Re W(m, 4b+q)
+// or Im W(m, 4b+q-4).  Product 2 (EPI 1) keeps the halves [Re | Im] above.
 // Each operand is held as BF16 pieces x = x_hi + x_lo; the GEMM accumulates
 // x_hi y_hi + x_hi y_lo + x_lo y_hi in FP32 in tensor memory (3 MMAs per slice).
 // Segments concatenate along k (product 1 has two: [dD | D0] [H | dH]^dagger).
@@ -304,6 +310,49 @@ __device__ __forceinline__ bool sk_wait_flag(const TcParams& P, int idx, volatil
 
 __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
+__device__ __forceinline__ uint4 pack8_bf16(const float (&x)[16], int h, float sgn) {
+  return make_uint4(pack_bf16(sgn * x[8 * h], sgn * x[8 * h + 1]), pack_bf16(sgn * x[8 * h + 2], sgn * x[8 * h + 3]),
+                    pack_bf16(sgn * x[8 * h + 4], sgn * x[8 * h + 5]), pack_bf16(sgn * x[8 * h + 6], sgn * x[8 * h + 7]));
+}
+
+// Product 1 epilogue: 32 accumulator columns gn .. gn + 31 of output row `row`
+// (gn a multiple of 32) in the interleaved order (4 Re, 4 Im per block of four W
+// columns) become 16 consecutive W columns j0 = gn / 2 .. j0 + 15, stored as the
+// embedded BF16 pieces of W that product 2 reads as its B operand: top row m =
+// [Re W | Im W], bottom row Np + m = [-Im W | Re W], hi at 0 and lo at 4 Np^2.
+__device__ __forceinline__ void store_w_pieces(__nv_bfloat16* W, int Np, int row, int gn, const uint32_t (&r)[32]) {
+  const long long ld = 2LL * Np, P1 = 4LL * Np * Np;
+  const int j0 = gn >> 1;
+  float re[16], im[16], rel[16], iml[16];
+#pragma unroll
+  for (int b = 0; b < 4; ++b)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      re[4 * b + q] = __uint_as_float(r[8 * b + q]);
+      im[4 * b + q] = __uint_as_float(r[8 * b + 4 + q]);
+    }
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    const float rh = __bfloat162float(__float2bfloat16_rn(re[i])), ih = __bfloat162float(__float2bfloat16_rn(im[i]));
+    rel[i] = re[i] - rh;
+    iml[i] = im[i] - ih;
+    re[i] = rh;
+    im[i] = ih;
+  }
+  const long long top = (long long)row * ld + j0, bot = (long long)(Np + row) * ld + j0;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    reinterpret_cast<uint4*>(W + top)[h] = pack8_bf16(re, h, 1.f);
+    reinterpret_cast<uint4*>(W + P1 + top)[h] = pack8_bf16(rel, h, 1.f);
+    reinterpret_cast<uint4*>(W + top + Np)[h] = pack8_bf16(im, h, 1.f);
+    reinterpret_cast<uint4*>(W + P1 + top + Np)[h] = pack8_bf16(iml, h, 1.f);
+    reinterpret_cast<uint4*>(W + bot)[h] = pack8_bf16(im, h, -1.f);
+    reinterpret_cast<uint4*>(W + P1 + bot)[h] = pack8_bf16(iml, h, -1.f);
+    reinterpret_cast<uint4*>(W + bot + Np)[h] = pack8_bf16(re, h, 1.f);
+    reinterpret_cast<uint4*>(W + P1 + bot + Np)[h] = pack8_bf16(rel, h, 1.f);
+  }
+}
+
 // ----------------------------------------------------------------------------
 // the kernel
 // ----------------------------------------------------------------------------
@@ -499,32 +548,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcPa
                 make_float4(__uint_as_float(r[4 * v]), __uint_as_float(r[4 * v + 1]), __uint_as_float(r[4 * v + 2]),
                             __uint_as_float(r[4 * v + 3]));
         } else {
-          // embedded pieces of W: top row m = [Wr | Wi] (same as out),
-          // bottom row Np+m = [-Wi | Wr] (column halves swapped, left half negated)
-          __nv_bfloat16* W = reinterpret_cast<__nv_bfloat16*>(pr.out);
-          const long long P1 = 4LL * Np * Np;
-          const bool imag = gn >= Np;
-          const long long top = row * ld + gn;
-          const long long bot = (long long)(Np + row) * ld + (imag ? gn - Np : gn + Np);
-          const float sgn = imag ? -1.f : 1.f;
-#pragma unroll
-          for (int v = 0; v < 4; ++v) {
-            uint32_t hi[4], lo[4], nhi[4], nlo[4];
-#pragma unroll
-            for (int w = 0; w < 4; ++w) {
-              const float a = __uint_as_float(r[8 * v + 2 * w]), b = __uint_as_float(r[8 * v + 2 * w + 1]);
-              const __nv_bfloat16 ah = __float2bfloat16_rn(a), bh = __float2bfloat16_rn(b);
-              const float al = a - __bfloat162float(ah), bl = b - __bfloat162float(bh);
-              hi[w] = pack_bf16(__bfloat162float(ah), __bfloat162float(bh));
-              lo[w] = pack_bf16(al, bl);
-              nhi[w] = pack_bf16(sgn * __bfloat162float(ah), sgn * __bfloat162float(bh));
-              nlo[w] = pack_bf16(sgn * al, sgn * bl);
-            }
-            reinterpret_cast<uint4*>(W + top)[v] = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-            reinterpret_cast<uint4*>(W + P1 + top)[v] = make_uint4(lo[0], lo[1], lo[2], lo[3]);
-            reinterpret_cast<uint4*>(W + bot)[v] = make_uint4(nhi[0], nhi[1], nhi[2], nhi[3]);
-            reinterpret_cast<uint4*>(W + P1 + bot)[v] = make_uint4(nlo[0], nlo[1], nlo[2], nlo[3]);
-          }
+          store_w_pieces(reinterpret_cast<__nv_bfloat16*>(pr.out), Np, row, gn, r);
         }
       }
       tc_fence_before();
@@ -816,30 +840,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm2(const __grid_constant__ TcP
                 make_float4(__uint_as_float(r[4 * v]), __uint_as_float(r[4 * v + 1]), __uint_as_float(r[4 * v + 2]),
                             __uint_as_float(r[4 * v + 3]));
         } else {
-          __nv_bfloat16* W = reinterpret_cast<__nv_bfloat16*>(pr.out);
-          const long long P1 = 4LL * Np * Np;
-          const bool imag = gn >= Np;
-          const long long top = row * ld + gn;
-          const long long bot = (long long)(Np + row) * ld + (imag ? gn - Np : gn + Np);
-          const float sgn = imag ? -1.f : 1.f;
-#pragma unroll
-          for (int v = 0; v < 4; ++v) {
-            uint32_t hi[4], lo[4], nhi[4], nlo[4];
-#pragma unroll
-            for (int w = 0; w < 4; ++w) {
-              const float a = __uint_as_float(r[8 * v + 2 * w]), b = __uint_as_float(r[8 * v + 2 * w + 1]);
-              const __nv_bfloat16 ah = __float2bfloat16_rn(a), bh = __float2bfloat16_rn(b);
-              const float al = a - __bfloat162float(ah), bl = b - __bfloat162float(bh);
-              hi[w] = pack_bf16(__bfloat162float(ah), __bfloat162float(bh));
-              lo[w] = pack_bf16(al, bl);
-              nhi[w] = pack_bf16(sgn * __bfloat162float(ah), sgn * __bfloat162float(bh));
-              nlo[w] = pack_bf16(sgn * al, sgn * bl);
-            }
-            reinterpret_cast<uint4*>(W + top)[v] = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-            reinterpret_cast<uint4*>(W + P1 + top)[v] = make_uint4(lo[0], lo[1], lo[2], lo[3]);
-            reinterpret_cast<uint4*>(W + bot)[v] = make_uint4(nhi[0], nhi[1], nhi[2], nhi[3]);
-            reinterpret_cast<uint4*>(W + P1 + bot)[v] = make_uint4(nlo[0], nlo[1], nlo[2], nlo[3]);
-          }
+          store_w_pieces(reinterpret_cast<__nv_bfloat16*>(pr.out), Np, row, gn, r);
         }
       }
       tc_fence_before();

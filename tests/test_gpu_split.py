@@ -116,7 +116,8 @@ def test_split_timeout_returns_error_and_context_recovers():
 @pytest.mark.parametrize("variant", [0, 5, 1])
 def test_zero_panel_skipping_matches_the_dense_product(variant):
     """Product 1 skips the k-panels in which a tile's rows of H and dH are zero
-    (512 atoms: 48 of 64 panels remain for 256-wide tiles, 36 for 128-wide).
+    (512 atoms, rows of H interleaved Re/Im in blocks of four: 36 of 64 panels remain
+    for 256-row tiles, 32 for 128-row tiles).
     Those panels contribute exact zeros, so with a classic schedule (2-SM pair
     256-wide tiles, variant 0; single-CTA 128-wide tiles, variant 5) the
     propagation equals the dense product (product1 = DENSE, same variant) bit for
