@@ -542,6 +542,13 @@ def native(args):
         cpu = with_1thread(cpu_baseline(args.cpu_steps), args.cpu_1thread_steps)
     if rank != 0:
         return
+    clocks_source = "sampled during the timed region"
+    if not clocks.get("samples") and steady and steady["clocks"].get("samples"):
+        # a short timed region can end before nvidia-smi's first 200 ms sample: take the
+        # record of the steady windows that follow it directly in the same process
+        clocks = dict(steady["clocks"])
+        clocks_source = (f"timed region ({ms:.1f} ms) shorter than the 200 ms sampling interval: sampled during "
+                         f"the {steady['windows']} steady windows of {steady['steps_per_window']} steps that follow it")
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "steps/s", "n_gpus": world, "steps": K,
         "warmup": W, "ms_per_step": round(step_ms, 4), "higher_is_better": True, "scaling": "weak",
@@ -577,7 +584,7 @@ def native(args):
         "batched": bat,
         "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": 6 * K + 2,
-        "clocks": clocks,
+        "clocks": clocks, "clocks_source": clocks_source,
     }
     print(json.dumps(line), flush=True)
 

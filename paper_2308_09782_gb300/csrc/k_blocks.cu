@@ -445,6 +445,10 @@ __global__ void __launch_bounds__(kSccThreads) k_scc_eps(const DevSys* __restric
   const int n = fixed_step >= 0 ? fixed_step : *step;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int I = b * kSccRows + warp;  // one warp per row of gamma
+  // A(t_n), read now so that the last CTA's serial tail does not wait for it
+  double An[3] = {0.0, 0.0, 0.0};
+  if (tid == 0 && T.af && T.A)
+    for (int a = 0; a < 3; ++a) An[a] = T.A[3 * n + a];
   if (lane == 0)
 #pragma unroll
     for (int i = 0; i < 6; ++i) red[warp][i] = 0.0;
@@ -526,7 +530,7 @@ __global__ void __launch_bounds__(kSccThreads) k_scc_eps(const DevSys* __restric
     }
     if (T.af) {
       constexpr double inv_c = 1.0 / kLight;
-      for (int a = 0; a < 3; ++a) T.af[a] = T.A ? (float)(T.A[3 * n + a] * inv_c) : 0.f;
+      for (int a = 0; a < 3; ++a) T.af[a] = (float)(An[a] * inv_c);
     }
     int st = 0;
     if (!isfinite(J0) || !isfinite(J1) || !isfinite(J2) || !isfinite(E) || !isfinite(v[5])) st |= ST_NONFINITE;
@@ -734,14 +738,14 @@ __global__ void __launch_bounds__(256, 4) k_phase_split(const DevSys* __restrict
   // A(t_n)/c and the shifts as FP32, prepared once per step by k_scc_eps: the
   // kernel issues no FP64 instruction (each costs a warp many FP32 issue slots)
   const float a0 = T.af[0], a1 = T.af[1], a2 = T.af[2];
-  const int I = S.tgt_I[U.tg], J = S.tgt_J[U.tg];
-  const int oi = S.orb_off[I], ni = S.orb_off[I + 1] - oi;
-  const int oj = S.orb_off[J], nj = S.orb_off[J + 1] - oj;
+  // the target's constants in two 16-byte records (one load each, no lookups)
+  const int4 t0 = S.tgt_p0[U.tg], t1 = S.tgt_p1[U.tg];
+  const int I = t0.x, J = t0.y, g0 = t0.z, g1 = t0.w;
+  const int oi = t1.x, oj = t1.y, ni = t1.z & 0xffff, nj = t1.w & 0xffff;
+  const bool vec = (t1.z >> 16) != 0;
   const int nel = ni * nj;
-  const int g0 = S.tgt_img0[U.tg], g1 = S.tgt_img0[U.tg + 1];
   const float beta = 0.5f * (T.epsf[I] + T.epsf[J]);
   const float dbeta = 0.5f * (T.depsf[I] + T.depsf[J]);
-  const bool vec = S.tgt_vec[U.tg] != 0;
   const long long dss = S.ds_stride;
   for (int k = 0; k < S.nk; ++k) {
     const DevItem& it = items[T.item0 + k];
@@ -756,7 +760,7 @@ __global__ void __launch_bounds__(256, 4) k_phase_split(const DevSys* __restrict
           const float4 dx = *reinterpret_cast<const float4*>(S.dsf + off);
           const float4 dy = *reinterpret_cast<const float4*>(S.dsf + dss + off);
           const float4 dz = *reinterpret_cast<const float4*>(S.dsf + 2 * dss + off);
-          const float2 ph = S.phasef[(long long)k * S.n_blk + S.img_blk[g]];
+          const float2 ph = S.phase_img[(long long)k * S.n_img + g];  // e^{-i 2 pi k.n} of image g
           const float s4[4] = {sv.x, sv.y, sv.z, sv.w}, h4[4] = {hv.x, hv.y, hv.z, hv.w};
           const float x4[4] = {dx.x, dx.y, dx.z, dx.w}, y4[4] = {dy.x, dy.y, dy.z, dy.w};
           const float z4[4] = {dz.x, dz.y, dz.z, dz.w};
@@ -794,7 +798,7 @@ __global__ void __launch_bounds__(256, 4) k_phase_split(const DevSys* __restrict
           const long long off = S.img_off[g] + e;
           const float sv = S.sf[off], hv = S.h0f[off];
           const float adS = a0 * S.dsf[off] + a1 * S.dsf[dss + off] + a2 * S.dsf[2 * dss + off];
-          const float2 ph = S.phasef[(long long)k * S.n_blk + S.img_blk[g]];
+          const float2 ph = S.phase_img[(long long)k * S.n_img + g];  // e^{-i 2 pi k.n} of image g
           const float vr = hv + beta * sv;
           hr += ph.x * vr - ph.y * adS;
           hi += ph.x * adS + ph.y * vr;

@@ -412,6 +412,31 @@ int prepare_system(vgtb_ctx* ctx, int si, const vgtb_system& s, HostSys& h, DevS
     }
     TRY(upload(ctx, &pi, vec.data(), vec.size()));
     d.tgt_vec = pi;
+    if (ctx->split) {
+      std::vector<int4> p0(h.n_tgt), p1(h.n_tgt);
+      for (int tg = 0; tg < h.n_tgt; ++tg) {
+        const int I = h.tgt_I[tg], J = h.tgt_J[tg];
+        p0[tg] = make_int4(I, J, h.tgt_img0[tg], h.tgt_img0[tg + 1]);
+        p1[tg] = make_int4(h.orb_off[I], h.orb_off[J], (h.orb_off[I + 1] - h.orb_off[I]) | (vec[tg] << 16),
+                           h.orb_off[J + 1] - h.orb_off[J]);
+      }
+      int4* p4;
+      TRY(upload(ctx, &p4, p0.data(), p0.size()));
+      d.tgt_p0 = p4;
+      TRY(upload(ctx, &p4, p1.data(), p1.size()));
+      d.tgt_p1 = p4;
+      const int n_img = (int)h.img_blk.size();
+      std::vector<float2> pim((size_t)h.nk * n_img);
+      for (int k = 0; k < h.nk; ++k)
+        for (int g = 0; g < n_img; ++g) {
+          const double2 v = ph[(size_t)k * s.n_blocks + h.img_blk[g]];
+          pim[(size_t)k * n_img + g] = make_float2((float)v.x, (float)v.y);
+        }
+      float2* pf2;
+      TRY(upload(ctx, &pf2, pim.data(), pim.size()));
+      d.phase_img = pf2;
+      d.n_img = n_img;
+    }
     // element offsets of the nonzeros (row-major within each target) and per-atom ranges
     if ((long long)h.Np * h.Np > 2147483647LL) return fail(ctx, VGTB_E_INVALID, "system %d: Np too large", si);
     std::vector<int> eoff(h.n_el), eat(h.nat + 1);

@@ -138,6 +138,12 @@ struct DevSys {
   const float2* phasef;    // [nk][n_blk]
   float* R0f;              // [nk][Np][2Np] planar
   float2* D0f;             // [nk][Np][Np] FP32 copy of D0 (split form, block-sparse first product)
+  // split-form phase build: per target {I, J, first image, end image} and
+  // {o_I, o_J, n_I | vec << 16, n_J}; the FP32 phase of every (k, image)
+  const int4* tgt_p0;      // [n_tgt]
+  const int4* tgt_p1;      // [n_tgt]
+  const float2* phase_img; // [nk][n_img]
+  int n_img;
 };
 
 struct DevTraj {
