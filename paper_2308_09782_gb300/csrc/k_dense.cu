@@ -237,12 +237,16 @@ void launch_leap(const LeapItem* items, int n_items, int Np_max, int x_f32, cons
 // copy (block-sparse product) and/or its BF16 hi/lo pieces (dense tcgen05
 // product).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256, 5) k_leap_split(const LeapItem* __restrict__ items, const int* step, double dt,
+// Thread layout: 16 x 16 threads, each owns two adjacent columns (2 tx, 2 tx + 1)
+// of rows ty and ty + 16 of a 32 x 32 tile, so R0 is read and the BF16 pieces
+// written two columns per instruction; X is staged as separate real and
+// imaginary tiles, whose transposed reads (X_ji) hit distinct banks.
+__global__ void __launch_bounds__(256, 4) k_leap_split(const LeapItem* __restrict__ items, const int* step, double dt,
                                                     int* counter, int* step_rw) {
   pdl_wait();
   pdl_trigger();
-  __shared__ float2 Xa[LT][LT + 1];
-  __shared__ float2 Xb[LT][LT + 1];
+  __shared__ float Xre[2][LT][LT + 1];  // [0] tile (bi, bj), [1] tile (bj, bi)
+  __shared__ float Xim[2][LT][LT + 1];
   const LeapItem& it = items[blockIdx.y];
   const int Np = it.Np;
   const int nt = Np / LT;
@@ -257,14 +261,25 @@ __global__ void __launch_bounds__(256, 5) k_leap_split(const LeapItem* __restric
     }
   }
   const int bj = bi + p;
-  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 16 x 16
+  const int c0 = 2 * tx;
   const float* X = (const float*)it.X;
   if (active) {
-    for (int r = ty; r < LT; r += 8) {
-      const long long ra = (long long)(bi * LT + r) * 2 * Np + bj * LT + tx;
-      const long long rb = (long long)(bj * LT + r) * 2 * Np + bi * LT + tx;
-      Xa[r][tx] = make_float2(X[ra], X[ra + Np]);
-      Xb[r][tx] = make_float2(X[rb], X[rb + Np]);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int r = ty + 16 * h;
+      const long long ra = (long long)(bi * LT + r) * 2 * Np + bj * LT + c0;
+      const long long rb = (long long)(bj * LT + r) * 2 * Np + bi * LT + c0;
+      const float2 ar = *reinterpret_cast<const float2*>(X + ra), ai = *reinterpret_cast<const float2*>(X + ra + Np);
+      const float2 br = *reinterpret_cast<const float2*>(X + rb), bim = *reinterpret_cast<const float2*>(X + rb + Np);
+      Xre[0][r][c0] = ar.x;
+      Xre[0][r][c0 + 1] = ar.y;
+      Xim[0][r][c0] = ai.x;
+      Xim[0][r][c0 + 1] = ai.y;
+      Xre[1][r][c0] = br.x;
+      Xre[1][r][c0 + 1] = br.y;
+      Xim[1][r][c0] = bim.x;
+      Xim[1][r][c0 + 1] = bim.y;
     }
   }
   __syncthreads();
@@ -274,41 +289,56 @@ __global__ void __launch_bounds__(256, 5) k_leap_split(const LeapItem* __restric
     const double coef = euler ? dt : 2.0 * dt;
     const double2* base = euler ? it.D[cur] : it.D[nxt];
     const long long P = 2LL * Np * Np;
-    constexpr int RPT = LT / 8;  // rows per thread
     for (int half = 0; half < (bi == bj ? 1 : 2); ++half) {
       const int gi0 = half == 0 ? bi : bj, gj0 = half == 0 ? bj : bi;
-      // all loads of the thread's rows first (D_{n-1} is overwritten in place,
+      const int A = half, B = half ^ 1;  // tile of (i, j) and of its mirror (j, i)
+      // all loads of the thread's elements first (D_{n-1} is overwritten in place,
       // element by element, by the same thread), then the updates and stores
-      float r0r[RPT], r0i[RPT];
-      double2 b[RPT];
+      float2 r0r[2], r0i[2];
+      double2 b[2][2];
 #pragma unroll
-      for (int j = 0; j < RPT; ++j) {
-        const int r = ty + 8 * j;
-        const long long idx = (long long)(gi0 * LT + r) * Np + gj0 * LT + tx;
-        const long long pr = (long long)(gi0 * LT + r) * 2 * Np + gj0 * LT + tx;
-        r0r[j] = it.R0f ? it.R0f[pr] : 0.f;
-        r0i[j] = it.R0f ? it.R0f[pr + Np] : 0.f;
-        b[j] = base[idx];
+      for (int h = 0; h < 2; ++h) {
+        const int r = ty + 16 * h;
+        const long long idx = (long long)(gi0 * LT + r) * Np + gj0 * LT + c0;
+        const long long pr = (long long)(gi0 * LT + r) * 2 * Np + gj0 * LT + c0;
+        r0r[h] = it.R0f ? *reinterpret_cast<const float2*>(it.R0f + pr) : make_float2(0.f, 0.f);
+        r0i[h] = it.R0f ? *reinterpret_cast<const float2*>(it.R0f + pr + Np) : make_float2(0.f, 0.f);
+        b[h][0] = base[idx];
+        b[h][1] = base[idx + 1];
       }
 #pragma unroll
-      for (int j = 0; j < RPT; ++j) {
-        const int r = ty + 8 * j;
-        const float2 xij = half == 0 ? Xa[r][tx] : Xb[r][tx];
-        const float2 xji = half == 0 ? Xb[tx][r] : Xa[tx][r];
-        const long long idx = (long long)(gi0 * LT + r) * Np + gj0 * LT + tx;
-        const long long pr = (long long)(gi0 * LT + r) * 2 * Np + gj0 * LT + tx;
-        const float dr = r0r[j] + (xij.y + xji.y);
-        const float di = r0i[j] + (-(xij.x - xji.x));
-        const double2 v = make_double2(fma(coef, f2d_bits(dr), b[j].x), fma(coef, f2d_bits(di), b[j].y));
-        it.D[nxt][idx] = v;
-        const float fr = d2f_bits(v.x), fi = d2f_bits(v.y);
-        if (it.f32) it.f32[idx] = make_float2(fr, fi);
+      for (int h = 0; h < 2; ++h) {
+        const int r = ty + 16 * h;
+        const long long idx = (long long)(gi0 * LT + r) * Np + gj0 * LT + c0;
+        const long long pr = (long long)(gi0 * LT + r) * 2 * Np + gj0 * LT + c0;
+        float fr[2], fi[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const int c = c0 + e;
+          const float xij_re = Xre[A][r][c], xij_im = Xim[A][r][c];
+          const float xji_re = Xre[B][c][r], xji_im = Xim[B][c][r];
+          const float dr = (e ? r0r[h].y : r0r[h].x) + (xij_im + xji_im);
+          const float di = (e ? r0i[h].y : r0i[h].x) + (-(xij_re - xji_re));
+          const double2 v = make_double2(fma(coef, f2d_bits(dr), b[h][e].x), fma(coef, f2d_bits(di), b[h][e].y));
+          it.D[nxt][idx + e] = v;
+          fr[e] = d2f_bits(v.x);
+          fi[e] = d2f_bits(v.y);
+        }
+        if (it.f32) *reinterpret_cast<float4*>(it.f32 + idx) = make_float4(fr[0], fi[0], fr[1], fi[1]);
         if (it.pieces) {
-          const __nv_bfloat16 rh = __float2bfloat16_rn(fr), ih = __float2bfloat16_rn(fi);
-          it.pieces[pr] = rh;
-          it.pieces[P + pr] = __float2bfloat16_rn(fr - __bfloat162float(rh));
-          it.pieces[pr + Np] = ih;
-          it.pieces[P + pr + Np] = __float2bfloat16_rn(fi - __bfloat162float(ih));
+          __nv_bfloat162 rh, rl, ih, il;
+          rh.x = __float2bfloat16_rn(fr[0]);
+          rh.y = __float2bfloat16_rn(fr[1]);
+          ih.x = __float2bfloat16_rn(fi[0]);
+          ih.y = __float2bfloat16_rn(fi[1]);
+          rl.x = __float2bfloat16_rn(fr[0] - __bfloat162float(rh.x));
+          rl.y = __float2bfloat16_rn(fr[1] - __bfloat162float(rh.y));
+          il.x = __float2bfloat16_rn(fi[0] - __bfloat162float(ih.x));
+          il.y = __float2bfloat16_rn(fi[1] - __bfloat162float(ih.y));
+          *reinterpret_cast<__nv_bfloat162*>(it.pieces + pr) = rh;
+          *reinterpret_cast<__nv_bfloat162*>(it.pieces + P + pr) = rl;
+          *reinterpret_cast<__nv_bfloat162*>(it.pieces + pr + Np) = ih;
+          *reinterpret_cast<__nv_bfloat162*>(it.pieces + P + pr + Np) = il;
         }
       }
     }
@@ -332,7 +362,7 @@ void launch_leap_split(const LeapItem* items, int n_items, int Np_max, const int
                        int* step_rw, cudaStream_t st) {
   const int nt = Np_max / LT;
   dim3 grid(nt * (nt + 1) / 2, n_items);
-  dim3 block(LT, 8);
+  dim3 block(LT / 2, LT / 2);
   launch_pdl(k_leap_split, grid, block, 0, st, items, step, dt, counter, step_rw);
 }
 
