@@ -747,7 +747,8 @@ __global__ void __launch_bounds__(256, 4) k_phase_split(const DevSys* __restrict
   const float beta = 0.5f * (T.epsf[I] + T.epsf[J]);
   const float dbeta = 0.5f * (T.depsf[I] + T.depsf[J]);
   const long long dss = S.ds_stride;
-  for (int k = 0; k < S.nk; ++k) {
+  // one k-point per grid row (blockIdx.y): the k-points of a target run in parallel
+  for (int k = blockIdx.y; k < S.nk; k += gridDim.y) {
     const DevItem& it = items[T.item0 + k];
     if (vec) {
       for (int r = sub; r < ni; r += 4) {
@@ -820,11 +821,11 @@ __global__ void __launch_bounds__(256, 4) k_phase_split(const DevSys* __restrict
 }
 
 void launch_phase_split(const DevSys* sys, const DevTraj* trj, const DevItem* items, const int* warp_prefix,
-                        int n_traj, int total_units, const int* step, cudaStream_t st) {
+                        int n_traj, int total_units, int max_nk, const int* step, cudaStream_t st) {
   (void)step;  // the level's operands come from k_scc_eps
   const int threads = 256;
   const int blocks = (total_units * 4 + threads - 1) / threads;
-  launch_pdl(k_phase_split, blocks, threads, 0, st, sys, trj, items, warp_prefix, n_traj, total_units);
+  launch_pdl(k_phase_split, dim3(blocks, max_nk), threads, 0, st, sys, trj, items, warp_prefix, n_traj, total_units);
 }
 
 // ---------------------------------------------------------------------------

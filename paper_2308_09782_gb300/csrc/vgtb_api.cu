@@ -96,7 +96,7 @@ struct vgtb_ctx {
   DevItem* d_items = nullptr;
   int* d_wpre = nullptr;
   int total_warps = 0;
-  int max_nat = 0, max_Np = 0;
+  int max_nat = 0, max_Np = 0, max_nk = 1;
   int* d_step = nullptr;
   int* d_counter = nullptr;
   int n_done = 0;
@@ -1011,7 +1011,8 @@ int enqueue_step(vgtb_ctx* ctx, cudaEvent_t* ev) {
   launch_obs_scc(ctx, ev, evflag, stride);
   if (ev) CK(cudaEventRecordWithFlags(ev[2], st, evflag));
   if (ctx->split)
-    launch_phase_split(ctx->d_sys, ctx->d_trj, ctx->d_items, ctx->d_wpre, nt, ctx->total_warps, ctx->d_step, st);
+    launch_phase_split(ctx->d_sys, ctx->d_trj, ctx->d_items, ctx->d_wpre, nt, ctx->total_warps, ctx->max_nk,
+                       ctx->d_step, st);
   else
     launch_phase(ctx->d_sys, ctx->d_trj, ctx->d_items, ctx->d_wpre, nt, ctx->total_warps, ctx->d_step,
                  ctx->delta ? PH_FP64_DELTA : PH_FP64_PLAIN, -1, st);
@@ -1197,6 +1198,7 @@ int vgtb_create_batch(vgtb_ctx** out, int n_sys, const vgtb_system* sys, int n_t
     rc = prepare_system(ctx, s, sys[s], ctx->sys[s], dsys[s], ctx->opt.init == VGTB_INIT_GROUND || ctx->cn);
     if (rc) return bail(rc);
     ctx->max_nocc = std::max(ctx->max_nocc, ctx->sys[s].nocc);
+    ctx->max_nk = std::max(ctx->max_nk, ctx->sys[s].nk);
     ctx->max_nat = std::max(ctx->max_nat, ctx->sys[s].nat);
     ctx->max_Np = std::max(ctx->max_Np, ctx->sys[s].Np);
   }

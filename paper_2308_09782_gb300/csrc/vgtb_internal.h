@@ -251,8 +251,9 @@ void launch_scc(const DevSys* sys, DevTraj* trj, int n_traj, const int* step, in
                 int fixed_step, int record, int max_nat, int atoms_done, cudaStream_t st);
 void launch_obs_atoms_split(const DevSys* sys, DevTraj* trj, const DevItem* items, int n_traj, int max_nat,
                             const int* step, int stride, int fixed_step, int record, cudaStream_t st);
+// grid rows = max_nk: row y builds k-points y, y + max_nk, ... of every target
 void launch_phase_split(const DevSys* sys, const DevTraj* trj, const DevItem* items, const int* warp_prefix,
-                        int n_traj, int total_units, const int* step, cudaStream_t st);
+                        int n_traj, int total_units, int max_nk, const int* step, cudaStream_t st);
 void launch_to_planar_f32(const double2* src, float* dst, int Np, cudaStream_t st);
 void launch_phase(const DevSys* sys, const DevTraj* trj, const DevItem* items, const int* warp_prefix,
                   int n_traj, int total_warps, const int* step, int mode, int fixed_step, cudaStream_t st);
