@@ -115,7 +115,8 @@ typedef struct {
   int tile_variant[2];      /* split form: tile variant of product 1 / product 2 (see
                                vgtb_tile_config; -1 = variant 0, or the autotuner's choice) */
   int product1;             /* form of the first product W = D H of Eq. 6 (VGTB_P1_*):
-                               AUTO (0, default): the FP64 path runs it block-sparse (below); the
+                               AUTO (0, default): the FP64 path runs it block-sparse (below), and
+                               so does the Crank-Nicolson integrator its product M = S^-1 H; the
                                split form runs the tcgen05 GEMM and skips the 64-wide k-panels in
                                which a tile's rows of H_k and dH_k are zero;
                                DENSE: a dense GEMM over all of H_k (8 N^3 flops; FP64 DFMA or

@@ -367,6 +367,105 @@ size_t bsr_p_smem_bytes(int max_grp_targets) {
   return (size_t)max_grp_targets * 128 + (size_t)kBsrStages * 4 * kBsrPThreads * sizeof(float2);
 }
 
+// ---------------------------------------------------------------------------
+// Crank-Nicolson density at the nonzero pattern (a sampled product):
+//   D[4J+c, 4K+r] = 2 sum_n conj(Cd[n, 4J+c]) Cd[n, 4K+r]   for every target (J, K)
+// with Cd = C^dagger ([nocc][Np]).  A CTA takes one group of 4 row atoms J (the
+// FP64 group tables of the block-sparse product) and walks the occupied states in
+// chunks of kCnChunk: the chunk's values at the group's own 16 columns and at the
+// columns of the union of its column atoms K are staged in shared memory, and
+// each thread accumulates up to kCnOut of the group's block elements in FP64.
+// 8 nnz(H) nocc flops instead of the 8 Np^2 nocc of the dense C C^dagger.
+// ---------------------------------------------------------------------------
+constexpr int kCnThreads = 256;
+constexpr int kCnChunk = 8;
+constexpr int kCnOut = 12;  // block elements per thread: up to 192 targets per group of 4 atoms
+
+size_t cn_smem_bytes(int max_ent) { return (size_t)kCnChunk * (16 + 4 * max_ent) * sizeof(double2); }
+
+__global__ void __launch_bounds__(kCnThreads) k_cn_density_pattern(const CnDensItem* __restrict__ items,
+                                                                  const BsrSys* __restrict__ sysv, int max_ent) {
+  extern __shared__ __align__(16) unsigned char cn_smem[];
+  double2* sJ = reinterpret_cast<double2*>(cn_smem);  // [kCnChunk][16]
+  double2* sK = sJ + kCnChunk * 16;                    // [kCnChunk][4 max_ent]
+  const int ldk = 4 * max_ent;
+  pdl_wait();
+  pdl_trigger();
+  const CnDensItem& it = items[blockIdx.y];
+  const BsrSys& S = sysv[it.sys];
+  const int g = blockIdx.x;
+  if (g >= S.n_grp) return;
+  const int Np = S.Np;
+  const int J0 = kBsrGroupF64 * g;
+  const int t0 = S.grp_t0[g], nt = S.grp_t0[g + 1] - t0;
+  const int e0 = S.grp_e0[g], ne = S.grp_e0[g + 1] - e0;
+  const int nout = 16 * nt;
+  // output u of this thread: target t0 + o / 16, element (c, r) = ((o % 16) / 4, o % 4)
+  int cj[kCnOut], ck[kCnOut];
+  double ar[kCnOut], ai[kCnOut];
+#pragma unroll
+  for (int u = 0; u < kCnOut; ++u) {
+    const int o = threadIdx.x + kCnThreads * u;
+    ar[u] = ai[u] = 0.0;
+    cj[u] = ck[u] = -1;
+    if (o < nout) {
+      const int code = S.tgt_ent[t0 + o / 16];
+      cj[u] = 4 * (code >> 10) + (o % 16) / 4;  // column of sJ
+      ck[u] = 4 * (code & 1023) + o % 4;         // column of sK
+    }
+  }
+  const double2* Cd = it.Cd;
+  for (int n0 = 0; n0 < it.nocc; n0 += kCnChunk) {
+    __syncthreads();  // the previous chunk's readers are done
+    for (int x = threadIdx.x; x < kCnChunk * 16; x += kCnThreads) {
+      const int nn = x >> 4, q = x & 15, n = n0 + nn, col = 4 * J0 + q;
+      sJ[x] = (n < it.nocc && col < Np) ? Cd[(long long)n * Np + col] : make_double2(0.0, 0.0);
+    }
+    for (int x = threadIdx.x; x < kCnChunk * 4 * ne; x += kCnThreads) {
+      const int nn = x / (4 * ne), q = x - nn * 4 * ne, n = n0 + nn;
+      const int col = 4 * __ldg(S.ent_K + e0 + (q >> 2)) + (q & 3);
+      sK[nn * ldk + q] = n < it.nocc ? Cd[(long long)n * Np + col] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < kCnOut; ++u) {
+      if (cj[u] < 0) continue;
+#pragma unroll
+      for (int nn = 0; nn < kCnChunk; ++nn) {
+        const double2 a = sJ[nn * 16 + cj[u]], b = sK[nn * ldk + ck[u]];
+        ar[u] = fma(a.x, b.x, fma(a.y, b.y, ar[u]));   // Re(conj(a) b)
+        ai[u] = fma(a.x, b.y, fma(-a.y, b.x, ai[u]));  // Im(conj(a) b)
+      }
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < kCnOut; ++u) {
+    if (cj[u] < 0) continue;
+    const int o = threadIdx.x + kCnThreads * u;
+    const int code = S.tgt_ent[t0 + o / 16];
+    const int row = 4 * (J0 + (code >> 10)) + (o % 16) / 4;
+    const int col = 4 * __ldg(S.ent_K + e0 + (code & 1023)) + o % 4;
+    it.D[(long long)row * Np + col] = make_double2(2.0 * ar[u], 2.0 * ai[u]);
+  }
+}
+
+int cn_density_max_targets() { return kCnThreads * kCnOut / 16; }
+
+int cn_density_configure(int max_ent) {
+  const size_t smem = cn_smem_bytes(max_ent);
+  if (smem > 227 * 1024) return -1;
+  return cudaFuncSetAttribute(k_cn_density_pattern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
+                 cudaSuccess
+             ? 0
+             : -1;
+}
+
+void launch_cn_density_pattern(const CnDensItem* items, const BsrSys* sys, int n_items, int max_groups, int max_ent,
+                               cudaStream_t st) {
+  launch_pdl(k_cn_density_pattern, dim3(max_groups, n_items), kCnThreads, cn_smem_bytes(max_ent), st, items, sys,
+             max_ent);
+}
+
 int bsr_group(int fp64) { return fp64 ? kBsrGroupF64 : kBsrGroupF32; }
 
 size_t bsr_smem_bytes(int fp64, int max_grp_targets) {

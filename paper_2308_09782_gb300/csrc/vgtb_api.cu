@@ -58,6 +58,7 @@ struct HostSys {
   float2* D0f = nullptr;    // split form, block-sparse first product: [nk][Np][Np] FP32 copy of D0
   int bsr_units = 0;        // block-sparse first product: CTAs per item (groups x column chunks)
   int bsr_tg_max = 0;       // most targets of one atom group
+  int bsr_ent_max = 0;      // most column atoms in the union of one atom group
 };
 
 struct HostTraj {
@@ -121,7 +122,9 @@ struct vgtb_ctx {
   BsrSys* d_bsrsys = nullptr;
   int* d_bsr_u0 = nullptr;   // [n_items+1] first unit of each item
   int* d_bsr_ctr = nullptr;  // [2] unit counter and finished-CTA counter
-  int bsr_units_max = 0, bsr_units_total = 0, bsr_tg_max = 0;
+  int bsr_units_max = 0, bsr_units_total = 0, bsr_tg_max = 0, bsr_ent_max = 0, bsr_grp_max = 0;
+  // Crank-Nicolson: D = 2 C C^dagger formed at H's nonzero pattern only for the step's sums
+  CnDensItem* d_cnd = nullptr;
   // graph
   cudaGraphExec_t graph = nullptr;
   int graph_steps = 0;
@@ -545,7 +548,7 @@ int build_bsr_tables(vgtb_ctx* ctx, HostSys& h, int fp64, BsrSys& b) {
   const int G = bsr_group(fp64);
   const int n_grp = (h.nat + G - 1) / G;
   std::vector<int> grp_t0(n_grp + 1), grp_e0(n_grp + 1, 0), ent_K;
-  std::vector<short> ent_slot;
+  std::vector<short> ent_slot, tgt_ent(h.n_tgt, 0);
   int tg_max = 0;
   for (int g = 0; g < n_grp; ++g) {
     const int J0 = g * G, J1 = std::min(h.nat, J0 + G);
@@ -561,10 +564,14 @@ int build_bsr_tables(vgtb_ctx* ctx, HostSys& h, int fp64, BsrSys& b) {
         v[J - J0] = (short)(t - t0);
       }
     for (auto& kv : uni) {
+      for (int j = 0; j < G; ++j)
+        if (kv.second[j] >= 0) tgt_ent[t0 + kv.second[j]] = (short)(1024 * j + (int)(ent_K.size() - grp_e0[g]));
       ent_K.push_back(kv.first);
       ent_slot.insert(ent_slot.end(), kv.second.begin(), kv.second.end());
     }
     grp_e0[g + 1] = (int)ent_K.size();
+    if (grp_e0[g + 1] - grp_e0[g] > 1023) return fail(ctx, VGTB_E_UNSUPPORTED, "atom group with over 1023 partners");
+    h.bsr_ent_max = std::max(h.bsr_ent_max, grp_e0[g + 1] - grp_e0[g]);
   }
   grp_t0[n_grp] = h.atom_tgt0[h.nat];
   memset(&b, 0, sizeof(b));
@@ -581,6 +588,8 @@ int build_bsr_tables(vgtb_ctx* ctx, HostSys& h, int fp64, BsrSys& b) {
   short* ps;
   TRY(upload(ctx, &ps, ent_slot.data(), ent_slot.size()));
   b.ent_slot = ps;
+  TRY(upload(ctx, &ps, tgt_ent.data(), tgt_ent.size()));
+  b.tgt_ent = ps;
   h.bsr_units = bsr_units(fp64, n_grp, h.Np);
   h.bsr_tg_max = tg_max;
   return VGTB_OK;
@@ -958,11 +967,20 @@ int build_cn_lists(vgtb_ctx* ctx) {
 //   into the last sweep -> convergence check -> step counter.
 // Event classes: obs (density product + sums), scc, phase, gemm1 (M), gemm2
 // (sweeps), leap (check + counter).
+// D_k = 2 C_k C_k^dagger for the charge, current and energy sums: at H's nonzero
+// pattern only when the sampled kernel is set up, else the dense product
+void launch_cn_density(vgtb_ctx* ctx, cudaStream_t st) {
+  if (ctx->d_cnd)
+    launch_cn_density_pattern(ctx->d_cnd, ctx->d_bsrsys, ctx->n_items, ctx->bsr_grp_max, ctx->bsr_ent_max, st);
+  else
+    launch_gemm_f64(ctx->d_gD, ctx->n_items, ctx->max_Np, ctx->max_Np, nullptr, st);
+}
+
 int enqueue_step_cn(vgtb_ctx* ctx, cudaEvent_t* ev, unsigned evflag) {
   cudaStream_t st = ctx->stream;
   const int nt = (int)ctx->trj.size();
   const int stride = ctx->opt.obs_stride > 0 ? ctx->opt.obs_stride : 1;
-  launch_gemm_f64(ctx->d_gD, ctx->n_items, ctx->max_Np, ctx->max_Np, nullptr, st);
+  launch_cn_density(ctx, st);
   launch_obs(ctx->d_sys, ctx->d_trj, ctx->d_items, ctx->d_wpre, nt, ctx->total_warps, ctx->d_step, 0, -1, st);
   if (ev) CK(cudaEventRecordWithFlags(ev[1], st, evflag));
   launch_scc(ctx->d_sys, ctx->d_trj, nt, ctx->d_step, stride, -1, 1, ctx->max_nat, 0, st);
@@ -970,7 +988,11 @@ int enqueue_step_cn(vgtb_ctx* ctx, cudaEvent_t* ev, unsigned evflag) {
   launch_phase(ctx->d_sys, ctx->d_trj, ctx->d_items, ctx->d_wpre, nt, ctx->total_warps, ctx->d_step, PH_FP64_CN, -1,
                st);
   if (ev) CK(cudaEventRecordWithFlags(ev[3], st, evflag));
-  launch_gemm_f64(ctx->d_gM, ctx->n_items, ctx->max_Np, ctx->max_Np, nullptr, st);
+  if (ctx->bsr)
+    launch_bsr(ctx->d_bsr, ctx->d_bsrsys, ctx->n_items, ctx->bsr_units_max, ctx->bsr_units_total, ctx->d_bsr_u0,
+               ctx->d_bsr_ctr, 1, ctx->bsr_tg_max, nullptr, st);
+  else
+    launch_gemm_f64(ctx->d_gM, ctx->n_items, ctx->max_Np, ctx->max_Np, nullptr, st);
   if (ev) CK(cudaEventRecordWithFlags(ev[4], st, evflag));
   for (GemmF64Item* g : ctx->sweep) launch_gemm_f64(g, ctx->n_items, ctx->max_nocc, ctx->max_Np, nullptr, st);
   if (ev) CK(cudaEventRecordWithFlags(ev[5], st, evflag));
@@ -1208,10 +1230,10 @@ int vgtb_create_batch(vgtb_ctx** out, int n_sys, const vgtb_system* sys, int n_t
   // the split form the dense tcgen05 product is faster at these sizes)
   bool blocks_ok = true;
   for (auto& h : ctx->sys) blocks_ok = blocks_ok && bsr_possible(h);
-  if (ctx->opt.product1 == VGTB_P1_BLOCKS && (!blocks_ok || ctx->cn))
-    return bail(fail(ctx, VGTB_E_UNSUPPORTED, "block-sparse first product needs 4 orbitals on every atom and the "
-                     "leapfrog integrator"));
-  ctx->bsr = !ctx->cn && blocks_ok &&
+  if (ctx->opt.product1 == VGTB_P1_BLOCKS && !blocks_ok)
+    return bail(fail(ctx, VGTB_E_UNSUPPORTED, "block-sparse first product needs 4 orbitals on every atom"));
+  // (Crank-Nicolson: the product M = S^-1 H of every step, FP64)
+  ctx->bsr = blocks_ok &&
              (ctx->opt.product1 == VGTB_P1_BLOCKS || (ctx->opt.product1 == VGTB_P1_AUTO && !ctx->split));
   std::vector<BsrSys> bsys(n_sys);
   if (ctx->bsr) {
@@ -1219,6 +1241,8 @@ int vgtb_create_batch(vgtb_ctx** out, int n_sys, const vgtb_system* sys, int n_t
       if ((rc = build_bsr_tables(ctx, ctx->sys[s], ctx->split ? 0 : 1, bsys[s]))) return bail(rc);
       ctx->bsr_units_max = std::max(ctx->bsr_units_max, ctx->sys[s].bsr_units);
       ctx->bsr_tg_max = std::max(ctx->bsr_tg_max, ctx->sys[s].bsr_tg_max);
+      ctx->bsr_ent_max = std::max(ctx->bsr_ent_max, ctx->sys[s].bsr_ent_max);
+      ctx->bsr_grp_max = std::max(ctx->bsr_grp_max, bsys[s].n_grp);
     }
     if (bsr_configure(ctx->split ? 0 : 1, ctx->bsr_tg_max))
       return bail(fail(ctx, VGTB_E_UNSUPPORTED, "block-sparse product: %d targets per atom group exceed shared memory",
@@ -1293,7 +1317,13 @@ int vgtb_create_batch(vgtb_ctx** out, int n_sys, const vgtb_system* sys, int n_t
         it.Xf = fam[T.sys].Xf + 2 * NN * li;
       } else if (ctx->cn) {
         const size_t nc = (size_t)h.nocc * h.Np;
-        if ((rc = dalloc(ctx, &it.H, NN))) return bail(rc);
+        if (ctx->bsr) {
+          double2* kh = nullptr;
+          if ((rc = dalloc(ctx, &kh, (size_t)h.n_el))) return bail(rc);
+          it.kH = kh;
+        } else if ((rc = dalloc(ctx, &it.H, NN))) {
+          return bail(rc);
+        }
         if ((rc = dalloc(ctx, &it.W, NN))) return bail(rc);
         if ((rc = dalloc(ctx, &it.Cd, nc))) return bail(rc);
         if ((rc = dalloc(ctx, &it.Y[0], nc))) return bail(rc);
@@ -1398,7 +1428,11 @@ int vgtb_create_batch(vgtb_ctx** out, int n_sys, const vgtb_system* sys, int n_t
       b.nseg = ctx->delta ? 2 : 1;
       b.R[0] = it.kH;
       b.R[1] = it.kdH;
-      if (ctx->split) {
+      if (ctx->cn) {
+        b.nseg = 1;                            // M = S^-1 H^dagger of the midpoint H
+        b.A[0] = h.Sinv + it.k * NN;
+        b.W = it.W;
+      } else if (ctx->split) {
         b.A[0] = it.dDf;                       // FP32 copy of the current dD level
         b.A[1] = h.D0f + it.k * NN;
         b.W = it.Wemb_p;
@@ -1416,6 +1450,14 @@ int vgtb_create_batch(vgtb_ctx** out, int n_sys, const vgtb_system* sys, int n_t
     ctx->bsr_units_total = u0[ctx->n_items];
     if ((rc = upload(ctx, &ctx->d_bsr_u0, u0.data(), u0.size()))) return bail(rc);
     if ((rc = dalloc(ctx, &ctx->d_bsr_ctr, 2))) return bail(rc);
+    if (ctx->cn && ctx->bsr_tg_max <= cn_density_max_targets() && cn_density_configure(ctx->bsr_ent_max) == 0) {
+      std::vector<CnDensItem> cd(ctx->n_items);
+      for (int i = 0; i < ctx->n_items; ++i) {
+        const DevItem& it = ctx->items_h[i];
+        cd[i] = CnDensItem{it.sys, it.Cd, it.D[0], ctx->sys[it.sys].nocc};
+      }
+      if ((rc = upload(ctx, &ctx->d_cnd, cd.data(), cd.size()))) return bail(rc);
+    }
   }
   // setup: S^-1, ground state
   for (int s = 0; s < n_sys; ++s) {
@@ -1593,7 +1635,7 @@ int vgtb_propagate(vgtb_ctx* ctx, int nsteps) {
   }
   // observables of the final level
   const int nt = (int)ctx->trj.size();
-  if (ctx->cn) launch_gemm_f64(ctx->d_gD, ctx->n_items, ctx->max_Np, ctx->max_Np, nullptr, ctx->stream);
+  if (ctx->cn) launch_cn_density(ctx, ctx->stream);
   if (ctx->cn) {
     launch_obs(ctx->d_sys, ctx->d_trj, ctx->d_items, ctx->d_wpre, nt, ctx->total_warps, ctx->d_step, 0, -1,
                ctx->stream);
@@ -1634,6 +1676,8 @@ int vgtb_get_density(vgtb_ctx* ctx, int t, int k, double* d_out) {
   const DevItem& it = ctx->items_h[T.item0 + k];
   const size_t NN = (size_t)h.Np * h.Np;
   const int cur = ctx->n_done & 1;
+  // Crank-Nicolson steps form D only at H's nonzero pattern: the whole D = 2 C C^dagger now
+  if (ctx->cn && ctx->d_cnd) launch_gemm_f64(ctx->d_gD, ctx->n_items, ctx->max_Np, ctx->max_Np, nullptr, ctx->stream);
   std::vector<double2> a(NN), b;
   CK(cudaMemcpyAsync(a.data(), it.D[cur], NN * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream));
   if (ctx->delta) {

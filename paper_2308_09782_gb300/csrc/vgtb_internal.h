@@ -205,6 +205,8 @@ struct BsrSys {
   const int* grp_e0;       // [n_grp+1] first union entry of each group
   const int* ent_K;        // [n_ent] column atom K of each entry
   const short* ent_slot;   // [n_ent][G] target index of (J_j, K) minus grp_t0, or -1
+  const short* tgt_ent;    // [n_tgt] 1024 x (row atom - first atom of its group) + position of the
+                           // column atom K in the group's union list
 };
 
 struct BsrItem {
@@ -218,6 +220,21 @@ int bsr_group(int fp64);
 size_t bsr_smem_bytes(int fp64, int max_grp_targets);
 int bsr_configure(int fp64, int max_grp_targets);
 int bsr_units(int fp64, int n_grp, int Np);  // CTAs per item
+
+// Crank-Nicolson: D_k = 2 C C^dagger at the nonzero pattern of H_k only (what
+// the charge, current and energy sums read), from C^dagger [nocc][Np] of every
+// item; uses the FP64 group tables of the block-sparse product.  D entries off
+// the pattern are left as they are.
+struct CnDensItem {
+  int sys;
+  const double2* Cd;       // [nocc][Np] occupied states as rows (C^dagger)
+  double2* D;              // [Np][Np]
+  int nocc;
+};
+int cn_density_configure(int max_ent);
+int cn_density_max_targets();  // most targets per atom group the kernel takes
+void launch_cn_density_pattern(const CnDensItem* items, const BsrSys* sys, int n_items, int max_groups, int max_ent,
+                               cudaStream_t st);
 // FP64: grid (max_units, n_items); split form: persistent CTAs taking units
 // 0..total_units-1 (item it owns item_u0[it] .. item_u0[it+1]-1) from the
 // counter pair ctr[2] (zero before the first launch; reset by each launch)

@@ -75,6 +75,27 @@ def test_cn_si64_pulse_vs_oracle():
         _compare(c, ref, sysd, gs["C"][0].shape[1])
 
 
+def test_cn_block_sparse_and_dense_m_agree():
+    """M = S^-1 H of every Crank-Nicolson step runs over H's nonzero atom blocks by
+    default and as a dense FP64 GEMM with product1 = DENSE: the same products up to
+    summation order, so the states agree to 1e-12 after 100 steps (si64, pulse),
+    and the dense run is within the oracle bounds too."""
+    from paper_2308_09782_gb300 import vgtb
+    name, n = "si64_pulse", 100
+    sysd, A, _ = system(name)
+    ctx, gs = oracle_ground(name)
+    n_occ = gs["C"][0].shape[1]
+    ref = cn.propagate_cn(sysd, A[:n + 1], n, gs["C"], ctx=ctx)
+    with _cn_ctx(sysd, gs["C"]) as a, _cn_ctx(sysd, gs["C"], product1=vgtb.P1_DENSE) as b:
+        for c in (a, b):
+            c.set_field(0, A[:n + 1])
+            c.propagate(n)
+        Ca = [a.get_coefficients(0, k, n_occ) for k in range(8)]
+        Cb = [b.get_coefficients(0, k, n_occ) for k in range(8)]
+        assert rel_fro(Ca, Cb) <= 1e-12
+        _compare(b, ref, sysd, n_occ)
+
+
 def test_cn_512_atoms_gamma_prefix():
     """512-atom Gamma kick (N = 2048, 1024 occupied states): 6 steps vs the oracle."""
     name, n = "si512_kick", 6
