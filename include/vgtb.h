@@ -252,9 +252,10 @@ int vgtb_kernel_stats(vgtb_ctx* ctx, long long* launches, double* ms, int n);
  * (product 1 = [dD|D0][H|dH]^dagger, product 2 = S^-1 W^dagger), chosen at
  * create (variant 0, or the autotuner's fastest).  cfg[4] = {tile width,
  * pipeline stages, schedule (0 classic, 1 stream-K, 2 whole waves classic and
- * stream-K over the rest; 4, 5, 6: the same with the k-panels skipped in which
- * the tile's rows of H_k and dH_k are zero, product 1 only), 1 if the tile spans
- * a 2-SM CTA pair}.  When the first product runs block-sparse
+ * stream-K over the rest; + 4: the k-panels skipped in which the tile's rows
+ * of H_k and dH_k are zero, product 1 only; + 8: classic over column tiles of
+ * planned widths, multiples of 16, the tile width being the widest), 1 if the
+ * tile spans a 2-SM CTA pair}.  When the first product runs block-sparse
  * (VGTB_P1_BLOCKS), product 1 reports {atoms per group, output rows per CTA, 3, 0}.
  * Errors: E_INVALID (product not 1 or 2, NULL), E_STATE (FP64 context). */
 int vgtb_tile_config(const vgtb_ctx* ctx, int product, int* cfg);

@@ -51,14 +51,19 @@ bool encode_map(CUtensorMap* m, const void* base, int cols, int rows, int batch,
 }
 
 struct Variant {
-  int bn, st, streamk, pair;
+  int bn, st, streamk, pair, widths;
 };
-// tile width (per CTA, or per pair for the 2-SM variant), pipeline stages,
-// schedule (0 classic, 1 stream-K over all tiles, 2 whole waves classic and
-// stream-K over the rest), 2-SM pair.  Variant 0 is the default; all are
+// tile width (per CTA, or per pair for the 2-SM variant; the largest width
+// with planned widths), pipeline stages, schedule (0 classic, 1 stream-K over
+// all tiles, 2 whole waves classic and stream-K over the rest), 2-SM pair,
+// column tiles (0: all bn wide; 1: the split of the 2 Np B rows into tiles of
+// near-equal widths, multiples of 16, with the shortest modelled time of the
+// longest worker, see plan_columns; 2: the same among splits into tiles at
+// least 192 wide, which re-read the A operand less often).  Variant 0 is the default; all are
 // autotune candidates.
-constexpr Variant kVariants[] = {{256, 3, 0, 1}, {256, 3, 1, 1}, {256, 3, 2, 1}, {256, 2, 0, 0},
-                                 {256, 2, 1, 0}, {128, 3, 0, 0}, {128, 3, 1, 0}};
+constexpr Variant kVariants[] = {{256, 3, 0, 1, 0}, {256, 3, 1, 1, 0}, {256, 3, 2, 1, 0}, {256, 2, 0, 0, 0},
+                                 {256, 2, 1, 0, 0}, {128, 3, 0, 0, 0}, {128, 3, 1, 0, 0}, {256, 3, 0, 1, 1},
+                                 {256, 3, 0, 1, 2}};
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
 template <int BN, int ST, int EPI>
@@ -135,9 +140,9 @@ int tc_gemm_supported() {
   return (maj == 10 && min == 3) ? 1 : 0;
 }
 
-// Nonzero k-panels of each B column tile of product 1 for system v (tile width
-// bw rows of the embedded [[Re H, Im H], [-Im H, Re H]], rows interleaved in
-// blocks of four: B row n' holds H row 4 (n' / 8) + n' % 4): a panel kt covers
+// Nonzero k-panels of each B column tile of product 1 for system v (tile nt =
+// B rows starts[nt] .. starts[nt+1]-1 of the embedded [[Re H, Im H], [-Im H, Re H]],
+// rows interleaved in blocks of four: B row n' holds H row 4 (n' / 8) + n' % 4): a panel kt covers
 // the 64 columns k' = 64 kt .. 64 kt + 63 of a segment, i.e. H columns k' (real
 // half) or k' - Np (imaginary half); it is nonzero for the tile when some H row
 // of the tile belongs to an atom I with a target (I, J) whose columns meet the
@@ -145,8 +150,8 @@ int tc_gemm_supported() {
 // uniform = true pads every tile's list with panels of zeros (in increasing
 // order) to the longest list, so that all tiles take the same number of
 // k-iterations, as the stream-K schedules need.
-static void zero_panel_lists(const TcSysView& v, int bw, bool uniform, std::vector<int>& kofs,
-                             std::vector<short>& kidx) {
+static void zero_panel_lists(const TcSysView& v, const std::vector<int>& starts, bool uniform,
+                             std::vector<int>& kofs, std::vector<short>& kidx) {
   const std::vector<int>& off = *v.orb_off;
   const int nat = (int)off.size() - 1, N = off[nat], Np = v.Np;
   const int npan = 2 * Np / BK;
@@ -155,12 +160,12 @@ static void zero_panel_lists(const TcSysView& v, int bw, bool uniform, std::vect
     for (int o = off[a]; o < off[a + 1]; ++o) atom_of[o] = a;
   std::vector<std::vector<int>> nbr(nat);
   for (size_t t = 0; t < v.tgt_I->size(); ++t) nbr[(*v.tgt_I)[t]].push_back((*v.tgt_J)[t]);
-  const int tiles_n = 2 * Np / bw;
+  const int tiles_n = (int)starts.size() - 1;
   std::vector<std::vector<char>> pans(tiles_n);
   size_t longest = 1;
   for (int nt = 0; nt < tiles_n; ++nt) {
     std::vector<char> atoms(nat, 0), pan(npan, 0);
-    for (int r = nt * bw; r < (nt + 1) * bw; ++r) {
+    for (int r = starts[nt]; r < starts[nt + 1]; ++r) {
       const int row = 4 * (r / 8) + (r % 4);
       if (row < N) atoms[atom_of[row]] = 1;
     }
@@ -196,12 +201,84 @@ static void zero_panel_lists(const TcSysView& v, int bw, bool uniform, std::vect
   }
 }
 
+// Longest-processing-time assignment of tiles with costs cost[i] to G workers:
+// each tile in decreasing cost goes to the worker with the least work so far.
+// Returns the worker lists as the classic schedule's tile order (worker c takes
+// tord[c], tord[c + G], ...; -1 ends a shorter list) and the modelled time of
+// the longest worker in *span.
+static std::vector<int> lpt_order(const std::vector<double>& cost, int G, double* span) {
+  std::vector<int> idx(cost.size());
+  for (size_t i = 0; i < idx.size(); ++i) idx[i] = (int)i;
+  std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  std::vector<std::vector<int>> lists(G);
+  std::vector<double> load(G, 0.0);
+  for (int i : idx) {
+    int c = 0;
+    for (int g = 1; g < G; ++g)
+      if (load[g] < load[c]) c = g;
+    lists[c].push_back(i);
+    load[c] += cost[i];
+  }
+  size_t depth = 0;
+  for (auto& l : lists) depth = std::max(depth, l.size());
+  std::vector<int> tord(depth * G, -1);
+  for (int c = 0; c < G; ++c)
+    for (size_t j = 0; j < lists[c].size(); ++j) tord[j * G + c] = lists[c][j];
+  if (span) *span = *std::max_element(load.begin(), load.end());
+  return tord;
+}
+
+// Modelled time of a tile in k-iterations of a 256-wide tile: its width share of
+// its k-iterations, plus a fixed cost per tile (pipeline start, epilogue tail).
+constexpr double kTileFixed = 2.0;
+static double tile_model(int w, int kt) { return w / 256.0 * kt + kTileFixed; }
+
+// 2 Np B rows split into n tiles of near-equal widths, multiples of 16
+static std::vector<int> even_split(int total, int n) {
+  const int units = total / 16, q = units / n, r = units % n;
+  std::vector<int> st(1, 0);
+  for (int i = 0; i < n; ++i) st.push_back(st.back() + 16 * (q + (i < r ? 1 : 0)));
+  return st;
+}
+
+// Column tiles of the 2-SM pair kernel for system v: of the splits of its 2 Np
+// B rows into n = 2Np/256 .. 2Np/96 tiles of near-equal widths (at most 256;
+// mode 2: at least 192), the one with the shortest modelled time of the longest
+// of G workers when all its tiles (n_items x tiles_m row tiles) are assigned
+// longest first.  With the zero k-panels skipped a tile's k-iterations are its
+// panel count.
+static std::vector<int> plan_columns(const TcSysView& v, bool skip, int nseg, int tiles_m, int G, int mode) {
+  const int total = 2 * v.Np, n0 = (total + 255) / 256;
+  std::vector<std::pair<double, int>> score;
+  for (int n = n0; n <= std::max(total / 96, n0); ++n) {
+    const std::vector<int> st = even_split(total, n);
+    if (mode == 2 && n > n0 && st[n] - st[n - 1] < 192) continue;
+    std::vector<int> kt(n, nseg * total / BK);
+    if (skip) {
+      std::vector<int> kofs;
+      std::vector<short> kidx;
+      zero_panel_lists(v, st, false, kofs, kidx);
+      for (int i = 0; i < n; ++i) kt[i] = nseg * (kofs[i + 1] - kofs[i]);
+    }
+    std::vector<double> cost;
+    for (int it = 0; it < v.n_items; ++it)
+      for (int i = 0; i < n; ++i)
+        for (int m = 0; m < tiles_m; ++m) cost.push_back(tile_model(st[i + 1] - st[i], kt[i]));
+    double span = 0;
+    lpt_order(cost, G, &span);
+    score.push_back({span, n});
+  }
+  std::stable_sort(score.begin(), score.end());
+  return even_split(total, score[0].second);
+}
+
 static int build_one(const std::vector<TcSysView>& sys, const std::vector<DevItem>& items, int epi, int variant,
                      long long timeout_ns, TcPlan* plan, std::string* msg) {
-  const int BNv = kVariants[variant].bn;
-  const bool pair = kVariants[variant].pair != 0;
-  const int bbox = pair ? BNv / 2 : BNv;  // B rows loaded by one CTA
+  const Variant& var = kVariants[variant];
+  const int BNv = var.bn;
+  const bool pair = var.pair != 0;
   const int tm_rows = pair ? 2 * BM : BM;  // output rows of one tile
+  const int nseg = epi == 0 ? 2 : 1;
   memset(&plan->P, 0, sizeof(plan->P));
   plan->epi = epi;
   plan->variant = variant;
@@ -209,6 +286,27 @@ static int build_one(const std::vector<TcSysView>& sys, const std::vector<DevIte
     *msg = "too many systems in one batch for the split form (max 4)";
     return -1;
   }
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int G_full = pair ? nsm / 2 : nsm;
+  // zero-panel skipping: product 1, every system's pattern known; the stream-K
+  // schedules get lists of one length per system (see zero_panel_lists)
+  bool skip = epi == 0;
+  const bool uniform = var.streamk != 0;
+  for (const TcSysView& v : sys) skip = skip && v.orb_off && v.tgt_I && v.tgt_J;
+  // column tiles of every system
+  std::vector<std::vector<int>> starts(sys.size());
+  int wmax = 0;
+  for (size_t s = 0; s < sys.size(); ++s) {
+    const int tiles_m = (sys[s].Np + tm_rows - 1) / tm_rows;
+    starts[s] = var.widths ? plan_columns(sys[s], skip, nseg, tiles_m, G_full, var.widths)
+                           : even_split(2 * sys[s].Np, 2 * sys[s].Np / BNv);
+    for (size_t i = 0; i + 1 < starts[s].size(); ++i) wmax = std::max(wmax, starts[s][i + 1] - starts[s][i]);
+  }
+  const int bbox = pair ? wmax / 2 : BNv;  // B rows loaded by one CTA
+  plan->wmax = wmax;
+  plan->P.b_rows = pair ? bbox : 0;
   for (size_t s = 0; s < sys.size(); ++s) {
     const TcSysView& v = sys[s];
     const int Np = v.Np;
@@ -222,19 +320,14 @@ static int build_one(const std::vector<TcSysView>& sys, const std::vector<DevIte
       if (!encode_map(&plan->P.mB[s][0], v.Wemb_p, 2 * Np, 2 * Np, v.n_items, bbox, msg)) return -1;
     }
   }
-  // zero-panel skipping: product 1, every system's pattern known; the stream-K
-  // schedules get lists of one length per system (see zero_panel_lists)
-  bool skip = epi == 0;
-  const bool uniform = kVariants[variant].streamk != 0;
-  for (const TcSysView& v : sys) skip = skip && v.orb_off && v.tgt_I && v.tgt_J;
-  std::vector<int> sys_kofs0(sys.size(), 0), sys_kidx0(sys.size(), 0), all_kofs;
+  std::vector<int> sys_kofs0(sys.size(), 0), sys_kidx0(sys.size(), 0), sys_cofs0(sys.size(), 0), all_kofs, all_cofs;
   std::vector<short> all_kidx;
   std::vector<std::vector<int>> sys_cnt(sys.size());
   if (skip) {
     for (size_t s = 0; s < sys.size(); ++s) {
       std::vector<int> kofs;
       std::vector<short> kidx;
-      zero_panel_lists(sys[s], BNv, uniform, kofs, kidx);
+      zero_panel_lists(sys[s], starts[s], uniform, kofs, kidx);
       sys_kofs0[s] = (int)all_kofs.size();
       sys_kidx0[s] = (int)all_kidx.size();
       for (size_t i = 0; i + 1 < kofs.size(); ++i) sys_cnt[s].push_back(kofs[i + 1] - kofs[i]);
@@ -250,19 +343,31 @@ static int build_one(const std::vector<TcSysView>& sys, const std::vector<DevIte
     cudaMemcpy(plan->d_kidx, all_kidx.data(), sizeof(short) * all_kidx.size(), cudaMemcpyHostToDevice);
     plan->skip = true;
   }
+  if (var.widths) {
+    for (size_t s = 0; s < sys.size(); ++s) {
+      sys_cofs0[s] = (int)all_cofs.size();
+      all_cofs.insert(all_cofs.end(), starts[s].begin(), starts[s].end());
+    }
+    if (cudaMalloc(&plan->d_cofs, sizeof(int) * all_cofs.size()) != cudaSuccess) {
+      *msg = "cudaMalloc failed for the column tiles";
+      return -1;
+    }
+    cudaMemcpy(plan->d_cofs, all_cofs.data(), sizeof(int) * all_cofs.size(), cudaMemcpyHostToDevice);
+  }
   std::vector<TcProb> probs;
   std::vector<int> local(sys.size(), 0);
-  std::vector<std::pair<int, int>> tile_cost;  // (k-panels, tile) for the longest-first order
+  std::vector<double> tile_cost;  // modelled time of every tile, for the longest-first order
   int tiles = 0;
   long long iters = 0;
   for (const DevItem& it : items) {
     const TcSysView& v = sys[it.sys];
+    const std::vector<int>& st = starts[it.sys];
     TcProb pr{};
     pr.sys = it.sys;
     const int li = local[it.sys]++;
     pr.Np = v.Np;
     pr.tiles_m = (v.Np + tm_rows - 1) / tm_rows;
-    pr.tiles_n = 2 * v.Np / BNv;
+    pr.tiles_n = (int)st.size() - 1;
     pr.tile0 = tiles;
     if (epi == 0) {
       pr.a_b[0] = li;
@@ -275,15 +380,17 @@ static int build_one(const std::vector<TcSysView>& sys, const std::vector<DevIte
       pr.b_b[0] = li;
       pr.out = it.Xf;
     }
-    pr.kt = (epi == 0 ? 2 : 1) * (2 * v.Np) / BK;
+    pr.kt = nseg * (2 * v.Np) / BK;
     pr.iter0 = (int)iters;
     if (skip) {
       pr.kofs = plan->d_kofs + sys_kofs0[it.sys];
       pr.kidx = plan->d_kidx + sys_kidx0[it.sys];
-      pr.kt = 2 * sys_cnt[it.sys][0];  // every segment takes the panel list (uniform lists: one length)
-      for (int nt = 0; nt < pr.tiles_n; ++nt)
-        for (int mt = 0; mt < pr.tiles_m; ++mt) tile_cost.push_back({sys_cnt[it.sys][nt], tiles + nt * pr.tiles_m + mt});
+      pr.kt = nseg * sys_cnt[it.sys][0];  // every segment takes the panel list (uniform lists: one length)
     }
+    if (var.widths) pr.cofs = plan->d_cofs + sys_cofs0[it.sys];
+    for (int nt = 0; nt < pr.tiles_n; ++nt)
+      for (int mt = 0; mt < pr.tiles_m; ++mt)
+        tile_cost.push_back(tile_model(st[nt + 1] - st[nt], skip ? nseg * sys_cnt[it.sys][nt] : pr.kt));
     tiles += pr.tiles_m * pr.tiles_n;
     iters += (long long)pr.tiles_m * pr.tiles_n * pr.kt;
     probs.push_back(pr);
@@ -295,33 +402,28 @@ static int build_one(const std::vector<TcSysView>& sys, const std::vector<DevIte
   }
   cudaMemcpy(plan->d_probs, probs.data(), sizeof(TcProb) * probs.size(), cudaMemcpyHostToDevice);
   cudaMemset(plan->d_err, 0, sizeof(int));
-  int dev = 0, nsm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  if (skip && !uniform) {
-    // tiles of unequal length: the workers take them longest first
-    std::stable_sort(tile_cost.begin(), tile_cost.end(),
-                     [](const std::pair<int, int>& a, const std::pair<int, int>& b) { return a.first > b.first; });
-    std::vector<int> tord(tile_cost.size());
-    for (size_t i = 0; i < tord.size(); ++i) tord[i] = tile_cost[i].second;
+  plan->P.probs = plan->d_probs;
+  plan->P.n_prob = (int)probs.size();
+  plan->P.total_tiles = tiles;
+  plan->P.nseg = nseg;
+  plan->P.err = plan->d_err;
+  plan->P.timeout_ns = timeout_ns;
+  plan->grid = std::min(tiles, nsm);
+  plan->smem = variant_smem(variant);
+  if (pair) plan->grid = 2 * std::min(tiles, nsm / 2);
+  if (!var.streamk && ((skip && !uniform) || var.widths)) {
+    // tiles of unequal cost: longest first, each to the least loaded worker
+    const std::vector<int> tord = lpt_order(tile_cost, pair ? plan->grid / 2 : plan->grid, nullptr);
     if (cudaMalloc(&plan->d_tord, sizeof(int) * tord.size()) != cudaSuccess) {
       *msg = "cudaMalloc failed for the tile order";
       return -1;
     }
     cudaMemcpy(plan->d_tord, tord.data(), sizeof(int) * tord.size(), cudaMemcpyHostToDevice);
     plan->P.tord = plan->d_tord;
+    plan->P.n_tord = (int)tord.size();
   }
-  plan->P.probs = plan->d_probs;
-  plan->P.n_prob = (int)probs.size();
-  plan->P.total_tiles = tiles;
-  plan->P.nseg = epi == 0 ? 2 : 1;
-  plan->P.err = plan->d_err;
-  plan->P.timeout_ns = timeout_ns;
-  plan->grid = std::min(tiles, nsm);
-  plan->smem = variant_smem(variant);
-  if (pair) plan->grid = 2 * std::min(tiles, nsm / 2);
   // stream-K needs every CTA to own at least one k-iteration; otherwise fall back
-  if (kVariants[variant].streamk && iters >= 2LL * nsm) {
+  if (var.streamk && iters >= 2LL * nsm) {
     plan->grid = pair ? (nsm & ~1) : nsm;  // pairs: workers are the nsm / 2 clusters
     plan->P.streamk = 1;
     plan->P.total_iters = iters;
@@ -331,7 +433,7 @@ static int build_one(const std::vector<TcSysView>& sys, const std::vector<DevIte
     const int G = pair ? plan->grid / 2 : plan->grid;
     int t0 = 0;
     long long i0 = 0;
-    if (kVariants[variant].streamk == 2) {
+    if (var.streamk == 2) {
       t0 = (tiles / G) * G;
       i0 = iters;
       for (const TcProb& pr : probs)
@@ -465,6 +567,7 @@ void tc_destroy_plan(TcPlan* p) {
   if (p->d_kofs) cudaFree(p->d_kofs);
   if (p->d_kidx) cudaFree(p->d_kidx);
   if (p->d_tord) cudaFree(p->d_tord);
+  if (p->d_cofs) cudaFree(p->d_cofs);
   delete p;
 }
 
@@ -473,6 +576,10 @@ int tc_plan_variant(const TcPlan* p) { return p ? p->variant : -1; }
 int tc_plan_info(const TcPlan* p, int* out4) {
   if (!p || tc_variant_info(p->variant, out4)) return -1;
   if (p->skip) out4[2] += 4;  // 4, 5, 6: the schedule with zero k-panels skipped
+  if (kVariants[p->variant].widths) {
+    out4[0] = p->wmax;        // the widest column tile
+    out4[2] += 8;             // 8, 12: classic over planned column widths
+  }
   return 0;
 }
 

@@ -16,7 +16,9 @@
 // x_hi y_hi + x_hi y_lo + x_lo y_hi in FP32 in tensor memory (3 MMAs per slice).
 // Segments concatenate along k (product 1 has two: [dD | D0] [H | dH]^dagger).
 //
-// Kernel: persistent CTAs over 128 x BN output tiles; warp 0 issues TMA loads
+// Kernel: persistent CTAs over 128 x BN output tiles (2-SM pair: 256 x w, with
+// the column tiles either all 256 wide or of planned widths w, multiples of 16,
+// that balance the tiles over the pairs); warp 0 issues TMA loads
 // (SWIZZLE_128B, 4-D maps: k, row, piece, batch) into a STAGES-deep ring,
 // warp 1 allocates tensor memory and issues tcgen05.mma from one thread,
 // warps 2-5 drain the double-buffered accumulator with tcgen05.ld and store
@@ -49,6 +51,10 @@ struct TcProb {
   // a nonzero are kidx[kofs[nt] .. kofs[nt+1]-1]; every segment uses the list
   const int* kofs;
   const short* kidx;
+  // 2-SM pair kernel, classic schedule: first B row of each column tile
+  // (tiles_n + 1 entries, the last 2 Np; widths multiples of 16 up to 256, so
+  // that the tiles can be balanced over the workers); null = tiles of 256
+  const int* cofs;
 };
 
 struct TcParams {
@@ -58,7 +64,10 @@ struct TcParams {
   int n_prob, total_tiles, nseg;
   int* err;
   long long timeout_ns;
-  const int* tord;     // classic schedule: order in which the workers take the tiles (null = 0, 1, ...)
+  const int* tord;     // classic schedule: worker c takes tiles tord[c], tord[c + G], ... (null = 0, 1, ...;
+                       // an entry -1 ends the worker's list)
+  int n_tord;          // entries of tord
+  int b_rows;          // 2-SM pair kernel: B rows per CTA in one TMA box (0 = 128)
   // stream-K schedule (streamk != 0): the tiles below sk_tile0 (whole waves)
   // go to the workers in turn, as in the classic schedule, so that workers on
   // the same operand rows stay at the same k and share them through L2; worker c
@@ -70,7 +79,7 @@ struct TcParams {
   int sk_tile0;
   long long sk_iter0;
   long long total_iters;
-  float* ws;           // [G][BM][BN]
+  float* ws;           // per CTA slot: [BN / 4][BM] float4 (see ws_slot)
   int* flags;          // [G], 1 = partial ready (reset to 0 by the finishing CTA)
 };
 
@@ -83,7 +92,8 @@ struct TcPlan {
   int* d_kofs = nullptr;    // zero-panel skipping: panel lists of every system, and the tile order
   short* d_kidx = nullptr;
   int* d_tord = nullptr;
-  int grid = 0, smem = 0, variant = 0, epi = 0;
+  int* d_cofs = nullptr;    // planned column tiles of every system
+  int grid = 0, smem = 0, variant = 0, epi = 0, wmax = 0;
   bool skip = false;
 };
 
@@ -231,6 +241,17 @@ __device__ __forceinline__ void tile_panel(const TcProb& pr, int t, int kk, int&
   kt = pr.kidx[k0 + kk - sg * cnt];
 }
 
+// first B row and width of column tile nt of the 2-SM pair kernel
+__device__ __forceinline__ void col_tile(const TcProb& pr, int nt, int& cb, int& w) {
+  if (pr.cofs) {
+    cb = pr.cofs[nt];
+    w = pr.cofs[nt + 1] - cb;
+  } else {
+    cb = nt * 256;
+    w = 256;
+  }
+}
+
 // Work units: classic mode walks whole tiles t = blockIdx.x + i G; stream-K
 // mode walks this CTA's k-iteration range, split at tile boundaries.  Every
 // role of the CTA runs the same cursor, so they agree on the sequence.
@@ -254,9 +275,10 @@ __device__ __forceinline__ void cursor_init(const TcParams& P, UnitCursor& u, in
 // next unit: global tile t, its k-iterations [kb, ke) out of KT; false when done
 __device__ __forceinline__ bool cursor_next(const TcParams& P, UnitCursor& u, int G, int& t, int& kb, int& ke,
                                             int& KT) {
-  const int t_classic = P.streamk ? P.sk_tile0 : P.total_tiles;
+  const int t_classic = P.streamk ? P.sk_tile0 : (P.tord ? P.n_tord : P.total_tiles);
   if (u.t_next < t_classic) {
     t = P.tord ? P.tord[u.t_next] : u.t_next;
+    if (t < 0) return false;
     u.t_next += G;
     u.p = P.tord ? find_prob_any(P.probs, P.n_prob, t) : find_prob(P.probs, P.n_prob, t, u.p);
     KT = tile_kt(P, P.probs[u.p], t);
@@ -308,6 +330,12 @@ __device__ __forceinline__ bool sk_wait_flag(const TcParams& P, int idx, volatil
   }
 }
 
+// Stream-K partial of CTA slot c (BM rows x bn FP32 columns): float4 j of row
+// rt at [j][rt], so that the 32 rows of a warp store and load 512 contiguous bytes.
+__device__ __forceinline__ float4* ws_slot(const TcParams& P, int c, int bn) {
+  return reinterpret_cast<float4*>(P.ws) + (size_t)c * BM * (bn / 4);
+}
+
 __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
 __device__ __forceinline__ uint4 pack8_bf16(const float (&x)[16], int h, float sgn) {
@@ -320,7 +348,9 @@ __device__ __forceinline__ uint4 pack8_bf16(const float (&x)[16], int h, float s
 // columns) become 16 consecutive W columns j0 = gn / 2 .. j0 + 15, stored as the
 // embedded BF16 pieces of W that product 2 reads as its B operand: top row m =
 // [Re W | Im W], bottom row Np + m = [-Im W | Re W], hi at 0 and lo at 4 Np^2.
-__device__ __forceinline__ void store_w_pieces(__nv_bfloat16* W, int Np, int row, int gn, const uint32_t (&r)[32]) {
+// (nh = 1: only the first 16 accumulator columns are the tile's, 8 W columns).
+__device__ __forceinline__ void store_w_pieces(__nv_bfloat16* W, int Np, int row, int gn, const uint32_t (&r)[32],
+                                               int nh) {
   const long long ld = 2LL * Np, P1 = 4LL * Np * Np;
   const int j0 = gn >> 1;
   float re[16], im[16], rel[16], iml[16];
@@ -342,6 +372,7 @@ __device__ __forceinline__ void store_w_pieces(__nv_bfloat16* W, int Np, int row
   const long long top = (long long)row * ld + j0, bot = (long long)(Np + row) * ld + j0;
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
+    if (h >= nh) break;
     reinterpret_cast<uint4*>(W + top)[h] = pack8_bf16(re, h, 1.f);
     reinterpret_cast<uint4*>(W + P1 + top)[h] = pack8_bf16(rel, h, 1.f);
     reinterpret_cast<uint4*>(W + top + Np)[h] = pack8_bf16(im, h, 1.f);
@@ -519,19 +550,19 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcPa
         TMEM_LD32(taddr, r);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         if (contrib) {
-          float4* w = reinterpret_cast<float4*>(P.ws + ((size_t)blockIdx.x * BM + rt) * BN + c0);
+          float4* w = ws_slot(P, blockIdx.x, BN) + (c0 / 4) * BM + rt;
 #pragma unroll
           for (int v = 0; v < 8; ++v)
-            w[v] = make_float4(__uint_as_float(r[4 * v]), __uint_as_float(r[4 * v + 1]), __uint_as_float(r[4 * v + 2]),
+            w[v * BM] = make_float4(__uint_as_float(r[4 * v]), __uint_as_float(r[4 * v + 1]), __uint_as_float(r[4 * v + 2]),
                                __uint_as_float(r[4 * v + 3]));
           continue;
         }
         if (finish) {
           for (int c2 = blockIdx.x + 1; c2 <= c_last; ++c2) {
-            const float4* w = reinterpret_cast<const float4*>(P.ws + ((size_t)c2 * BM + rt) * BN + c0);
+            const float4* w = ws_slot(P, c2, BN) + (c0 / 4) * BM + rt;
 #pragma unroll
             for (int v = 0; v < 8; ++v) {
-              const float4 f = __ldcg(w + v);
+              const float4 f = __ldcg(w + v * BM);
               r[4 * v] = __float_as_uint(__uint_as_float(r[4 * v]) + f.x);
               r[4 * v + 1] = __float_as_uint(__uint_as_float(r[4 * v + 1]) + f.y);
               r[4 * v + 2] = __float_as_uint(__uint_as_float(r[4 * v + 2]) + f.z);
@@ -548,7 +579,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcPa
                 make_float4(__uint_as_float(r[4 * v]), __uint_as_float(r[4 * v + 1]), __uint_as_float(r[4 * v + 2]),
                             __uint_as_float(r[4 * v + 3]));
         } else {
-          store_w_pieces(reinterpret_cast<__nv_bfloat16*>(pr.out), Np, row, gn, r);
+          store_w_pieces(reinterpret_cast<__nv_bfloat16*>(pr.out), Np, row, gn, r, 2);
         }
       }
       tc_fence_before();
@@ -640,7 +671,8 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm2(const __grid_constant__ TcP
   constexpr uint32_t B_BYTES = (BNP / 2) * BK * 2;          // this CTA's half of B, per piece
   constexpr uint32_t STAGE = 2 * A_BYTES + 2 * B_BYTES;
   constexpr uint32_t TCOLS = 2 * BNP;
-  constexpr uint32_t IDESC = idesc_bf16(2 * BM, BNP);
+  // bytes of one stage that the TMA copies (both pieces of A and of this CTA's B rows)
+  const uint32_t stage_tx = 2 * A_BYTES + 2 * (uint32_t)(P.b_rows ? P.b_rows : BNP / 2) * BK * 2;
   extern __shared__ uint8_t smraw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + ST * STAGE);
@@ -694,7 +726,9 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm2(const __grid_constant__ TcP
         const TcProb& pr = P.probs[cur.p];
         const int local = t - pr.tile0;
         const int mt = local % pr.tiles_m, nt = local / pr.tiles_m;
-        const int arow = mt * (2 * BM) + rank * BM, brow = nt * BNP + rank * (BNP / 2);
+        int cb, w;
+        col_tile(pr, nt, cb, w);
+        const int arow = mt * (2 * BM) + rank * BM, brow = cb + rank * (w / 2);
         for (int kk = kb; kk < ke; ++kk, ++it) {
           int sg, kt;
           tile_panel(pr, t, kk, sg, kt);
@@ -706,7 +740,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm2(const __grid_constant__ TcP
             break;
           }
           const uint32_t base = smem_u32(sm + s * STAGE);
-          if (leader_cta) mbar_expect_tx(full0 + 8 * s, 2 * STAGE);
+          if (leader_cta) mbar_expect_tx(full0 + 8 * s, 2 * stage_tx);
           const uint32_t fb = full_l + 8 * s;
           tma_load_4d_pair(base, ma, kt * BK, arow, 0, pr.a_b[sg], fb);
           tma_load_4d_pair(base + A_BYTES, ma, kt * BK, arow, 1, pr.a_b[sg], fb);
@@ -742,6 +776,12 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm2(const __grid_constant__ TcP
         }
         tc_fence_after();
         const uint32_t d = tmem + ab * BNP;
+        int cb, w;
+        {
+          const TcProb& pr = P.probs[cur.p];
+          col_tile(pr, (t - pr.tile0) / pr.tiles_m, cb, w);
+        }
+        const uint32_t idesc = idesc_bf16(2 * BM, w);
         for (int kk = kb; kk < ke; ++kk, ++it) {
           const int s = it % ST, r = it / ST;
           if (!mbar_wait(full0 + 8 * s, r & 1, P.timeout_ns, abort_flag, P.err)) {
@@ -756,9 +796,9 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm2(const __grid_constant__ TcP
             const uint64_t al = sw128_desc(base + A_BYTES + 32 * j);
             const uint64_t bh = sw128_desc(base + 2 * A_BYTES + 32 * j);
             const uint64_t bl = sw128_desc(base + 2 * A_BYTES + B_BYTES + 32 * j);
-            tc_mma_pair(d, ah, bh, IDESC, (kk > kb || j > 0) ? 1u : 0u);
-            tc_mma_pair(d, ah, bl, IDESC, 1u);
-            tc_mma_pair(d, al, bh, IDESC, 1u);
+            tc_mma_pair(d, ah, bh, idesc, (kk > kb || j > 0) ? 1u : 0u);
+            tc_mma_pair(d, ah, bl, idesc, 1u);
+            tc_mma_pair(d, al, bh, idesc, 1u);
           }
           tc_commit_pair(empty0 + 8 * s, 3);
           issued = true;
@@ -803,26 +843,28 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm2(const __grid_constant__ TcP
       const long long ld = 2LL * Np;
       const int rt = q * 32 + lane;
       const int row = mt * (2 * BM) + rank * BM + rt;
+      int cb, w;
+      col_tile(pr, nt, cb, w);
 #pragma unroll 1
-      for (int c0 = 0; c0 < BNP; c0 += 32) {
+      for (int c0 = 0; c0 < w; c0 += 32) {
         uint32_t r[32];
         const uint32_t taddr = tmem + ab * BNP + c0 + ((uint32_t)(q * 32) << 16);
         TMEM_LD32(taddr, r);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         if (contrib) {
-          float4* w = reinterpret_cast<float4*>(P.ws + ((size_t)me * BM + rt) * BNP + c0);
+          float4* wp = ws_slot(P, me, BNP) + (c0 / 4) * BM + rt;
 #pragma unroll
           for (int v = 0; v < 8; ++v)
-            w[v] = make_float4(__uint_as_float(r[4 * v]), __uint_as_float(r[4 * v + 1]), __uint_as_float(r[4 * v + 2]),
+            wp[v * BM] = make_float4(__uint_as_float(r[4 * v]), __uint_as_float(r[4 * v + 1]), __uint_as_float(r[4 * v + 2]),
                                __uint_as_float(r[4 * v + 3]));
           continue;
         }
         if (finish) {
           for (int p2 = pair + 1; p2 <= p_last; ++p2) {
-            const float4* w = reinterpret_cast<const float4*>(P.ws + ((size_t)(2 * p2 + rank) * BM + rt) * BNP + c0);
+            const float4* wp = ws_slot(P, 2 * p2 + (int)rank, BNP) + (c0 / 4) * BM + rt;
 #pragma unroll
             for (int v = 0; v < 8; ++v) {
-              const float4 f = __ldcg(w + v);
+              const float4 f = __ldcg(wp + v * BM);
               r[4 * v] = __float_as_uint(__uint_as_float(r[4 * v]) + f.x);
               r[4 * v + 1] = __float_as_uint(__uint_as_float(r[4 * v + 1]) + f.y);
               r[4 * v + 2] = __float_as_uint(__uint_as_float(r[4 * v + 2]) + f.z);
@@ -830,17 +872,19 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm2(const __grid_constant__ TcP
             }
           }
         }
-        const int gn = nt * BNP + c0;
+        const int gn = cb + c0;
+        const int nv = w - c0 < 32 ? w - c0 : 32;  // 16 in the last chunk of a width 32 m + 16
         if (row >= Np) continue;  // last row tile of an Np that is not a multiple of 256
         if (EPI == 1) {
           float* X = reinterpret_cast<float*>(pr.out) + row * ld + gn;
 #pragma unroll
           for (int v = 0; v < 8; ++v)
-            reinterpret_cast<float4*>(X)[v] =
-                make_float4(__uint_as_float(r[4 * v]), __uint_as_float(r[4 * v + 1]), __uint_as_float(r[4 * v + 2]),
-                            __uint_as_float(r[4 * v + 3]));
+            if (4 * v < nv)
+              reinterpret_cast<float4*>(X)[v] =
+                  make_float4(__uint_as_float(r[4 * v]), __uint_as_float(r[4 * v + 1]),
+                              __uint_as_float(r[4 * v + 2]), __uint_as_float(r[4 * v + 3]));
         } else {
-          store_w_pieces(reinterpret_cast<__nv_bfloat16*>(pr.out), Np, row, gn, r);
+          store_w_pieces(reinterpret_cast<__nv_bfloat16*>(pr.out), Np, row, gn, r, nv >> 4);
         }
       }
       tc_fence_before();

@@ -110,6 +110,7 @@ __global__ void k_na_prob(TcProb* prob, int* err, int Np, float* out) {
   p.iter0 = 0;
   p.kofs = nullptr;  // every k-panel
   p.kidx = nullptr;
+  p.cofs = nullptr;  // column tiles of 256
   *prob = p;
   *err = 0;
 }

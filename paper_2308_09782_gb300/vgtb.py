@@ -336,10 +336,12 @@ class Context:
         self._check(load().vgtb_tile_config(self._h, int(product), cfg))
         if cfg[2] == 3:
             return {"schedule": "block-sparse", "atoms_per_group": cfg[0], "rows_per_cta": cfg[1]}
-        return {"tile_n": cfg[0], "stages": cfg[1],
-                "schedule": ("classic", "stream-K", "classic waves + stream-K", "block-sparse",
-                             "classic, zero k-panels skipped", "stream-K, zero k-panels skipped",
-                             "classic waves + stream-K, zero k-panels skipped")[cfg[2]], "pair": bool(cfg[3])}
+        base = ("classic", "stream-K", "classic waves + stream-K")[cfg[2] & 3]
+        if cfg[2] & 8:
+            base += ", planned column widths"
+        if cfg[2] & 4:
+            base += ", zero k-panels skipped"
+        return {"tile_n": cfg[0], "stages": cfg[1], "schedule": base, "pair": bool(cfg[3])}
 
     def kernel_stats(self):
         n = len(KERNEL_CLASSES)
