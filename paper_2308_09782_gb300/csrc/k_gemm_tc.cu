@@ -26,8 +26,10 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
   return fn;
 }
 
-// 4-D BF16 map: (cols, rows, 2 pieces, batch), box (64, box_rows, 1, 1), 128B swizzle
-bool encode_map(CUtensorMap* m, const void* base, int cols, int rows, int batch, int box_rows, std::string* msg) {
+// 4-D BF16 map: (cols, rows, 2 pieces, batch), box (64 / kh, box_rows, 1, 1),
+// 128-byte swizzle (kh = 1) or 64-byte swizzle (kh = 2)
+bool encode_map(CUtensorMap* m, const void* base, int cols, int rows, int batch, int box_rows, std::string* msg,
+                int kh = 1) {
   auto enc = get_encode();
   if (!enc) {
     *msg = "cuTensorMapEncodeTiled unavailable";
@@ -35,10 +37,11 @@ bool encode_map(CUtensorMap* m, const void* base, int cols, int rows, int batch,
   }
   cuuint64_t dims[4] = {(cuuint64_t)cols, (cuuint64_t)rows, 2, (cuuint64_t)batch};
   cuuint64_t strides[3] = {(cuuint64_t)cols * 2, (cuuint64_t)cols * rows * 2, (cuuint64_t)cols * rows * 4};
-  cuuint32_t box[4] = {(cuuint32_t)BK, (cuuint32_t)box_rows, 1, 1};
+  cuuint32_t box[4] = {(cuuint32_t)(BK / kh), (cuuint32_t)box_rows, 1, 1};
   cuuint32_t es[4] = {1, 1, 1, 1};
   CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(base), dims, strides, box, es,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, kh == 2 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     char b[128];
@@ -51,7 +54,7 @@ bool encode_map(CUtensorMap* m, const void* base, int cols, int rows, int batch,
 }
 
 struct Variant {
-  int bn, st, streamk, pair, widths;
+  int bn, st, streamk, pair, widths, kh;
 };
 // tile width (per CTA, or per pair for the 2-SM variant; the largest width
 // with planned widths), pipeline stages, schedule (0 classic, 1 stream-K over
@@ -59,11 +62,14 @@ struct Variant {
 // column tiles (0: all bn wide; 1: the split of the 2 Np B rows into tiles of
 // near-equal widths, multiples of 16, with the shortest modelled time of the
 // longest worker, see plan_columns; 2: the same among splits into tiles at
-// least 192 wide, which re-read the A operand less often).  Variant 0 is the default; all are
+// least 192 wide, which re-read the A operand less often), k-slices per 64-wide
+// panel (1: stages of 64 columns; 2: stages of 32 columns, 7 of them, for the
+// pair kernel).  Variant 0 is the default; all are
 // autotune candidates.
-constexpr Variant kVariants[] = {{256, 3, 0, 1, 0}, {256, 3, 1, 1, 0}, {256, 3, 2, 1, 0}, {256, 2, 0, 0, 0},
-                                 {256, 2, 1, 0, 0}, {128, 3, 0, 0, 0}, {128, 3, 1, 0, 0}, {256, 3, 0, 1, 1},
-                                 {256, 3, 0, 1, 2}};
+constexpr Variant kVariants[] = {{256, 3, 0, 1, 0, 1}, {256, 3, 1, 1, 0, 1}, {256, 3, 2, 1, 0, 1},
+                                 {256, 2, 0, 0, 0, 1}, {256, 2, 1, 0, 0, 1}, {128, 3, 0, 0, 0, 1},
+                                 {128, 3, 1, 0, 0, 1}, {256, 3, 0, 1, 1, 1}, {256, 3, 0, 1, 2, 1},
+                                 {256, 7, 0, 1, 0, 2}, {256, 7, 0, 1, 1, 2}, {256, 7, 1, 1, 0, 2}};
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
 template <int BN, int ST, int EPI>
@@ -76,12 +82,12 @@ cudaError_t launch_t(const TcPlan* p, cudaStream_t st) {
   return launch_pdl(k_tc_gemm<BN, ST, EPI>, p->grid, 192, p->smem, st, p->P);
 }
 
-template <int ST, int EPI>
+template <int ST, int KH>
 int smem_pair() {
-  return ST * (2 * BM * BK * 2 + 2 * 128 * BK * 2) + 1024 + 256;
+  return ST * (2 * BM * (BK / KH) * 2 + 2 * 128 * (BK / KH) * 2) + 1024 + 256;
 }
 
-template <int ST, int EPI>
+template <int ST, int EPI, int KH>
 cudaError_t launch_pair(const TcPlan* p, cudaStream_t st) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(p->grid, 1, 1);
@@ -97,7 +103,7 @@ cudaError_t launch_pair(const TcPlan* p, cudaStream_t st) {
   attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 2;
-  return cudaLaunchKernelEx(&cfg, k_tc_gemm2<ST, EPI>, p->P);
+  return cudaLaunchKernelEx(&cfg, k_tc_gemm2<ST, EPI, KH>, p->P);
 }
 
 template <int BN, int ST, int EPI>
@@ -107,14 +113,18 @@ cudaError_t configure_t() {
 }
 
 cudaError_t launch_variant(const TcPlan* p, cudaStream_t st) {
-  if (kVariants[p->variant].pair) return p->epi == 0 ? launch_pair<3, 0>(p, st) : launch_pair<3, 1>(p, st);
+  if (kVariants[p->variant].pair) {
+    if (kVariants[p->variant].kh == 2)
+      return p->epi == 0 ? launch_pair<7, 0, 2>(p, st) : launch_pair<7, 1, 2>(p, st);
+    return p->epi == 0 ? launch_pair<3, 0, 1>(p, st) : launch_pair<3, 1, 1>(p, st);
+  }
   const bool wide = kVariants[p->variant].bn == 256;
   if (p->epi == 0) return wide ? launch_t<256, 2, 0>(p, st) : launch_t<128, 3, 0>(p, st);
   return wide ? launch_t<256, 2, 1>(p, st) : launch_t<128, 3, 1>(p, st);
 }
 
 int variant_smem(int v) {
-  if (kVariants[v].pair) return smem_pair<3, 0>();
+  if (kVariants[v].pair) return kVariants[v].kh == 2 ? smem_pair<7, 2>() : smem_pair<3, 1>();
   return kVariants[v].bn == 256 ? smem_bytes<256, 2, 0>() : smem_bytes<128, 3, 0>();
 }
 
@@ -124,10 +134,16 @@ cudaError_t configure_all() {
   if ((e = configure_t<128, 3, 0>()) != cudaSuccess) return e;
   if ((e = configure_t<256, 2, 1>()) != cudaSuccess) return e;
   if ((e = configure_t<128, 3, 1>()) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(k_tc_gemm2<3, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_pair<3, 0>())) !=
-      cudaSuccess)
+  if ((e = cudaFuncSetAttribute(k_tc_gemm2<3, 0, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                smem_pair<3, 1>())) != cudaSuccess)
     return e;
-  return cudaFuncSetAttribute(k_tc_gemm2<3, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_pair<3, 1>());
+  if ((e = cudaFuncSetAttribute(k_tc_gemm2<3, 1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                smem_pair<3, 1>())) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(k_tc_gemm2<7, 0, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                smem_pair<7, 2>())) != cudaSuccess)
+    return e;
+  return cudaFuncSetAttribute(k_tc_gemm2<7, 1, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_pair<7, 2>());
 }
 
 }  // namespace
@@ -311,13 +327,13 @@ static int build_one(const std::vector<TcSysView>& sys, const std::vector<DevIte
     const TcSysView& v = sys[s];
     const int Np = v.Np;
     if (epi == 0) {
-      if (!encode_map(&plan->P.mA[s][0], v.dD_p, 2 * Np, Np, v.n_items, BM, msg)) return -1;
-      if (!encode_map(&plan->P.mA[s][1], v.D0_p, 2 * Np, Np, v.nk, BM, msg)) return -1;
-      if (!encode_map(&plan->P.mB[s][0], v.Hemb_p, 2 * Np, 2 * Np, v.n_items, bbox, msg)) return -1;
-      if (!encode_map(&plan->P.mB[s][1], v.dHemb_p, 2 * Np, 2 * Np, v.n_items, bbox, msg)) return -1;
+      if (!encode_map(&plan->P.mA[s][0], v.dD_p, 2 * Np, Np, v.n_items, BM, msg, var.kh)) return -1;
+      if (!encode_map(&plan->P.mA[s][1], v.D0_p, 2 * Np, Np, v.nk, BM, msg, var.kh)) return -1;
+      if (!encode_map(&plan->P.mB[s][0], v.Hemb_p, 2 * Np, 2 * Np, v.n_items, bbox, msg, var.kh)) return -1;
+      if (!encode_map(&plan->P.mB[s][1], v.dHemb_p, 2 * Np, 2 * Np, v.n_items, bbox, msg, var.kh)) return -1;
     } else {
-      if (!encode_map(&plan->P.mA[s][0], v.Sinv_p, 2 * Np, Np, v.nk, BM, msg)) return -1;
-      if (!encode_map(&plan->P.mB[s][0], v.Wemb_p, 2 * Np, 2 * Np, v.n_items, bbox, msg)) return -1;
+      if (!encode_map(&plan->P.mA[s][0], v.Sinv_p, 2 * Np, Np, v.nk, BM, msg, var.kh)) return -1;
+      if (!encode_map(&plan->P.mB[s][0], v.Wemb_p, 2 * Np, 2 * Np, v.n_items, bbox, msg, var.kh)) return -1;
     }
   }
   std::vector<int> sys_kofs0(sys.size(), 0), sys_kidx0(sys.size(), 0), sys_cofs0(sys.size(), 0), all_kofs, all_cofs;

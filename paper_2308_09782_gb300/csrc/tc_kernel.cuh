@@ -185,6 +185,18 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
   return d;
 }
 
+// The same for a 64-byte swizzle (rows of 32 BF16): 8-row groups 512 bytes
+// apart, layout type 4 (SWIZZLE_64B).
+__device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(512 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)4 << 61;
+  return d;
+}
+
 // Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major.
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
@@ -664,15 +676,19 @@ __device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar_cluster) {
   asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar_cluster) : "memory");
 }
 
-template <int ST, int EPI>
+// KH = 1: one pipeline stage per 64-wide k-panel (128-byte swizzle); KH = 2:
+// two stages of 32 columns per panel (64-byte swizzle), so that twice as many
+// stages fit and the copies run further ahead of the MMAs.
+template <int ST, int EPI, int KH>
 __global__ void __launch_bounds__(192, 1) k_tc_gemm2(const __grid_constant__ TcParams P) {
   constexpr int BNP = 256;                                  // pair tile width
-  constexpr uint32_t A_BYTES = BM * BK * 2;                 // this CTA's 128 rows of A, per piece
-  constexpr uint32_t B_BYTES = (BNP / 2) * BK * 2;          // this CTA's half of B, per piece
+  constexpr int BKS = BK / KH;                              // k-columns per stage
+  constexpr uint32_t A_BYTES = BM * BKS * 2;                // this CTA's 128 rows of A, per piece
+  constexpr uint32_t B_BYTES = (BNP / 2) * BKS * 2;         // this CTA's half of B, per piece
   constexpr uint32_t STAGE = 2 * A_BYTES + 2 * B_BYTES;
   constexpr uint32_t TCOLS = 2 * BNP;
   // bytes of one stage that the TMA copies (both pieces of A and of this CTA's B rows)
-  const uint32_t stage_tx = 2 * A_BYTES + 2 * (uint32_t)(P.b_rows ? P.b_rows : BNP / 2) * BK * 2;
+  const uint32_t stage_tx = 2 * A_BYTES + 2 * (uint32_t)(P.b_rows ? P.b_rows : BNP / 2) * BKS * 2;
   extern __shared__ uint8_t smraw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + ST * STAGE);
@@ -729,23 +745,27 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm2(const __grid_constant__ TcP
         int cb, w;
         col_tile(pr, nt, cb, w);
         const int arow = mt * (2 * BM) + rank * BM, brow = cb + rank * (w / 2);
-        for (int kk = kb; kk < ke; ++kk, ++it) {
+        for (int kk = kb; ok && kk < ke; ++kk) {
           int sg, kt;
           tile_panel(pr, t, kk, sg, kt);
           const CUtensorMap* ma = &P.mA[pr.sys][sg];
           const CUtensorMap* mb = &P.mB[pr.sys][sg];
-          const int s = it % ST, r = it / ST;
-          if (!mbar_wait(empty0 + 8 * s, (r & 1) ^ 1, P.timeout_ns, abort_flag, P.err)) {
-            ok = false;
-            break;
+#pragma unroll 1
+          for (int h = 0; h < KH; ++h, ++it) {
+            const int s = it % ST, r = it / ST;
+            if (!mbar_wait(empty0 + 8 * s, (r & 1) ^ 1, P.timeout_ns, abort_flag, P.err)) {
+              ok = false;
+              break;
+            }
+            const uint32_t base = smem_u32(sm + s * STAGE);
+            if (leader_cta) mbar_expect_tx(full0 + 8 * s, 2 * stage_tx);
+            const uint32_t fb = full_l + 8 * s;
+            const int x = kt * BK + h * BKS;
+            tma_load_4d_pair(base, ma, x, arow, 0, pr.a_b[sg], fb);
+            tma_load_4d_pair(base + A_BYTES, ma, x, arow, 1, pr.a_b[sg], fb);
+            tma_load_4d_pair(base + 2 * A_BYTES, mb, x, brow, 0, pr.b_b[sg], fb);
+            tma_load_4d_pair(base + 2 * A_BYTES + B_BYTES, mb, x, brow, 1, pr.b_b[sg], fb);
           }
-          const uint32_t base = smem_u32(sm + s * STAGE);
-          if (leader_cta) mbar_expect_tx(full0 + 8 * s, 2 * stage_tx);
-          const uint32_t fb = full_l + 8 * s;
-          tma_load_4d_pair(base, ma, kt * BK, arow, 0, pr.a_b[sg], fb);
-          tma_load_4d_pair(base + A_BYTES, ma, kt * BK, arow, 1, pr.a_b[sg], fb);
-          tma_load_4d_pair(base + 2 * A_BYTES, mb, kt * BK, brow, 0, pr.b_b[sg], fb);
-          tma_load_4d_pair(base + 2 * A_BYTES + B_BYTES, mb, kt * BK, brow, 1, pr.b_b[sg], fb);
         }
       }
       if (!ok) {
@@ -782,7 +802,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm2(const __grid_constant__ TcP
           col_tile(pr, (t - pr.tile0) / pr.tiles_m, cb, w);
         }
         const uint32_t idesc = idesc_bf16(2 * BM, w);
-        for (int kk = kb; kk < ke; ++kk, ++it) {
+        for (int ks = kb * KH; ks < ke * KH; ++ks, ++it) {
           const int s = it % ST, r = it / ST;
           if (!mbar_wait(full0 + 8 * s, r & 1, P.timeout_ns, abort_flag, P.err)) {
             ok = false;
@@ -791,12 +811,14 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm2(const __grid_constant__ TcP
           tc_fence_after();
           const uint32_t base = smem_u32(sm + s * STAGE);
 #pragma unroll
-          for (int j = 0; j < BK / 16; ++j) {
-            const uint64_t ah = sw128_desc(base + 32 * j);
-            const uint64_t al = sw128_desc(base + A_BYTES + 32 * j);
-            const uint64_t bh = sw128_desc(base + 2 * A_BYTES + 32 * j);
-            const uint64_t bl = sw128_desc(base + 2 * A_BYTES + B_BYTES + 32 * j);
-            tc_mma_pair(d, ah, bh, idesc, (kk > kb || j > 0) ? 1u : 0u);
+          for (int j = 0; j < BKS / 16; ++j) {
+            const uint64_t ah = KH == 1 ? sw128_desc(base + 32 * j) : sw64_desc(base + 32 * j);
+            const uint64_t al = KH == 1 ? sw128_desc(base + A_BYTES + 32 * j) : sw64_desc(base + A_BYTES + 32 * j);
+            const uint64_t bh =
+                KH == 1 ? sw128_desc(base + 2 * A_BYTES + 32 * j) : sw64_desc(base + 2 * A_BYTES + 32 * j);
+            const uint64_t bl = KH == 1 ? sw128_desc(base + 2 * A_BYTES + B_BYTES + 32 * j)
+                                        : sw64_desc(base + 2 * A_BYTES + B_BYTES + 32 * j);
+            tc_mma_pair(d, ah, bh, idesc, (ks > kb * KH || j > 0) ? 1u : 0u);
             tc_mma_pair(d, ah, bl, idesc, 1u);
             tc_mma_pair(d, al, bh, idesc, 1u);
           }
