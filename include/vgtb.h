@@ -129,6 +129,12 @@ typedef struct {
                                the charges at every step; VGTB_SCC_FROZEN: H keeps the shift of
                                D_k(0) at every step (non-self-consistent propagation); charges,
                                current and energy are still evaluated from D_k(t_n) */
+  int chain;                /* split form, both products on the tcgen05 kernel: VGTB_CHAIN_AUTO (0,
+                               default) runs them as one launch, with a product-2 tile starting
+                               as soon as the rows of W it reads are stored (Eq. 6: X = S^-1 W^dagger
+                               needs W only), when that is faster at create than two launches;
+                               VGTB_CHAIN_OFF: two launches; VGTB_CHAIN_ON: one launch whenever
+                               the tile variants allow it (2-SM pairs, classic schedules) */
 } vgtb_options;
 
 #define VGTB_P1_AUTO     0
@@ -136,6 +142,9 @@ typedef struct {
 #define VGTB_P1_BLOCKS   2
 #define VGTB_SCC_ON      0
 #define VGTB_SCC_FROZEN  1
+#define VGTB_CHAIN_AUTO  0
+#define VGTB_CHAIN_OFF   1
+#define VGTB_CHAIN_ON    2
 
 /* Fill *opt with the defaults above (precision FP64, ground-state init, leapfrog). */
 void vgtb_default_options(vgtb_options* opt);
@@ -254,8 +263,8 @@ int vgtb_kernel_stats(vgtb_ctx* ctx, long long* launches, double* ms, int n);
  * pipeline stages, schedule (0 classic, 1 stream-K, 2 whole waves classic and
  * stream-K over the rest; + 4: the k-panels skipped in which the tile's rows
  * of H_k and dH_k are zero, product 1 only; + 8: classic over column tiles of
- * planned widths, multiples of 16, the tile width being the widest), 1 if the
- * tile spans a 2-SM CTA pair}.  When the first product runs block-sparse
+ * planned widths, multiples of 16, the tile width being the widest; + 16: both
+ * products run as one launch, VGTB_CHAIN_*), 1 if the tile spans a 2-SM CTA pair}.  When the first product runs block-sparse
  * (VGTB_P1_BLOCKS), product 1 reports {atoms per group, output rows per CTA, 3, 0}.
  * Errors: E_INVALID (product not 1 or 2, NULL), E_STATE (FP64 context). */
 int vgtb_tile_config(const vgtb_ctx* ctx, int product, int* cfg);

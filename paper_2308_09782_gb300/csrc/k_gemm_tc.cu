@@ -5,7 +5,7 @@
 #include <cstdio>
 #include <cstring>
 
-#include "tc_kernel.cuh"
+#include "tc_chain.cuh"
 
 namespace vgtb {
 
@@ -143,7 +143,10 @@ cudaError_t configure_all() {
   if ((e = cudaFuncSetAttribute(k_tc_gemm2<7, 0, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 smem_pair<7, 2>())) != cudaSuccess)
     return e;
-  return cudaFuncSetAttribute(k_tc_gemm2<7, 1, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_pair<7, 2>());
+  if ((e = cudaFuncSetAttribute(k_tc_gemm2<7, 1, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                smem_pair<7, 2>())) != cudaSuccess)
+    return e;
+  return cudaFuncSetAttribute(k_tc_chain<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_pair<3, 1>());
 }
 
 }  // namespace
@@ -418,6 +421,9 @@ static int build_one(const std::vector<TcSysView>& sys, const std::vector<DevIte
   }
   cudaMemcpy(plan->d_probs, probs.data(), sizeof(TcProb) * probs.size(), cudaMemcpyHostToDevice);
   cudaMemset(plan->d_err, 0, sizeof(int));
+  plan->probs_h = probs;
+  plan->starts_h = starts;
+  plan->cost_h = tile_cost;
   plan->P.probs = plan->d_probs;
   plan->P.n_prob = (int)probs.size();
   plan->P.total_tiles = tiles;
@@ -589,6 +595,10 @@ void tc_destroy_plan(TcPlan* p) {
 
 int tc_plan_variant(const TcPlan* p) { return p ? p->variant : -1; }
 
+void tc_clear_error(TcPlan* p) {
+  if (p) cudaMemset(p->d_err, 0, sizeof(int));
+}
+
 int tc_plan_info(const TcPlan* p, int* out4) {
   if (!p || tc_variant_info(p->variant, out4)) return -1;
   if (p->skip) out4[2] += 4;  // 4, 5, 6: the schedule with zero k-panels skipped
@@ -597,6 +607,234 @@ int tc_plan_info(const TcPlan* p, int* out4) {
     out4[2] += 8;             // 8, 12: classic over planned column widths
   }
   return 0;
+}
+
+// ----------------------------------------------------------------------------
+// chained schedule (tc_chain.cuh)
+// ----------------------------------------------------------------------------
+struct TcChain {
+  TcChainExtra X{};
+  const TcPlan* p1 = nullptr;  // not owned
+  const TcPlan* p2 = nullptr;
+  int* d_ord = nullptr;
+  int* d_blk0 = nullptr;
+  unsigned long long* d_ready = nullptr;
+  unsigned long long* d_epoch = nullptr;
+  int grid = 0, smem = 0;
+};
+
+bool tc_chainable(const TcPlan* p1, const TcPlan* p2) {
+  if (!p1 || !p2) return false;
+  const Variant& a = kVariants[p1->variant];
+  const Variant& b = kVariants[p2->variant];
+  return a.pair && b.pair && !a.streamk && !b.streamk && a.kh == 1 && b.kh == 1 &&
+         p1->probs_h.size() == p2->probs_h.size();
+}
+
+// The order of the units over G workers, by list scheduling on the modelled
+// tile times: product 1 tiles block by block (problem, 256-row block, column
+// tile), each to the worker free first; then product 2 tiles by the time at
+// which the blocks of W they read are complete (then longest first), each to
+// the worker free first, starting no earlier than that time.
+static std::vector<int> chain_order(const TcPlan* p1, const TcPlan* p2, int G, double* span) {
+  const std::vector<TcProb>& q1 = p1->probs_h;
+  const std::vector<TcProb>& q2 = p2->probs_h;
+  std::vector<double> avail(G, 0.0);
+  std::vector<std::vector<int>> lists(G);
+  auto take = [&](double ready, double cost, int unit) {
+    int c = 0;
+    for (int g = 1; g < G; ++g)
+      if (avail[g] < avail[c]) c = g;
+    const double start = std::max(avail[c], ready);
+    avail[c] = start + cost;
+    lists[c].push_back(unit);
+    return avail[c];
+  };
+  std::vector<std::vector<double>> blk_done(q1.size());
+  for (size_t p = 0; p < q1.size(); ++p) {
+    const TcProb& pr = q1[p];
+    blk_done[p].assign(pr.tiles_m, 0.0);
+    for (int mt = 0; mt < pr.tiles_m; ++mt)
+      for (int nt = 0; nt < pr.tiles_n; ++nt) {
+        const int t = pr.tile0 + nt * pr.tiles_m + mt;
+        blk_done[p][mt] = std::max(blk_done[p][mt], take(0.0, p1->cost_h[t], t));
+      }
+  }
+  struct U2 {
+    double ready, cost;
+    int unit;
+  };
+  std::vector<U2> u2;
+  const int t1 = p1->P.total_tiles;
+  for (size_t p = 0; p < q2.size(); ++p) {
+    const TcProb& pr = q2[p];
+    const std::vector<int>& st = p2->starts_h[pr.sys];
+    const int Np = pr.Np;
+    for (int nt = 0; nt < pr.tiles_n; ++nt) {
+      const int cb = st[nt], w = st[nt + 1] - st[nt];
+      double ready = 0.0;
+      const int seg[2][2] = {{cb, std::min(cb + w, Np)}, {std::max(cb, Np) - Np, cb + w - Np}};
+      for (auto& sg : seg)
+        if (sg[1] > sg[0])
+          for (int b = sg[0] / 256; b <= (sg[1] - 1) / 256; ++b) ready = std::max(ready, blk_done[p][b]);
+      for (int mt = 0; mt < pr.tiles_m; ++mt) {
+        const int t = pr.tile0 + nt * pr.tiles_m + mt;
+        u2.push_back({ready, p2->cost_h[t], t1 + t});
+      }
+    }
+  }
+  std::stable_sort(u2.begin(), u2.end(), [](const U2& a, const U2& b) {
+    return a.ready < b.ready || (a.ready == b.ready && a.cost > b.cost);
+  });
+  for (const U2& u : u2) take(u.ready, u.cost, u.unit);
+  size_t depth = 0;
+  for (auto& l : lists) depth = std::max(depth, l.size());
+  std::vector<int> ord(depth * G, -1);
+  for (int c = 0; c < G; ++c)
+    for (size_t j = 0; j < lists[c].size(); ++j) ord[j * G + c] = lists[c][j];
+  if (span) *span = *std::max_element(avail.begin(), avail.end());
+  return ord;
+}
+
+int tc_build_chain(const TcPlan* p1, const TcPlan* p2, TcChain** out, std::string* msg) {
+  *out = nullptr;
+  if (!tc_chainable(p1, p2)) {
+    *msg = "the two products cannot be chained (2-SM pair, classic schedule and 64-column stages needed)";
+    return -1;
+  }
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  // every pair must be resident at once (a product 2 tile may wait for a tile of
+  // any other pair): at most the clusters of two that fit on the device
+  int G = std::max(1, std::min(nsm / 2, std::max(p1->P.total_tiles, p2->P.total_tiles)));
+  {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * G, 1, 1);
+    cfg.blockDim = dim3(192, 1, 1);
+    cfg.dynamicSmemBytes = smem_pair<3, 1>();
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int maxc = 0;
+    if (cudaOccupancyMaxActiveClusters(&maxc, k_tc_chain<3>, &cfg) != cudaSuccess || maxc < 1) {
+      *msg = "cannot query the resident clusters of the chained kernel";
+      return -1;
+    }
+    G = std::min(G, maxc);
+  }
+  TcChain* c = new TcChain();
+  c->p1 = p1;
+  c->p2 = p2;
+  c->grid = 2 * G;
+  c->smem = smem_pair<3, 1>();
+  const std::vector<int> ord = chain_order(p1, p2, G, nullptr);
+  std::vector<int> blk0;
+  int nblk = 0;
+  for (const TcProb& pr : p1->probs_h) {
+    blk0.push_back(nblk);
+    nblk += pr.tiles_m;
+  }
+  if (cudaMalloc(&c->d_ord, sizeof(int) * ord.size()) != cudaSuccess ||
+      cudaMalloc(&c->d_blk0, sizeof(int) * blk0.size()) != cudaSuccess ||
+      cudaMalloc(&c->d_ready, sizeof(unsigned long long) * nblk) != cudaSuccess ||
+      cudaMalloc(&c->d_epoch, 2 * sizeof(unsigned long long)) != cudaSuccess) {
+    tc_destroy_chain(c);
+    *msg = "cudaMalloc failed for the chained schedule";
+    return -1;
+  }
+  cudaMemcpy(c->d_ord, ord.data(), sizeof(int) * ord.size(), cudaMemcpyHostToDevice);
+  cudaMemcpy(c->d_blk0, blk0.data(), sizeof(int) * blk0.size(), cudaMemcpyHostToDevice);
+  cudaMemset(c->d_ready, 0, sizeof(unsigned long long) * nblk);
+  cudaMemset(c->d_epoch, 0, 2 * sizeof(unsigned long long));
+  c->X.ord = c->d_ord;
+  c->X.n_ord = (int)ord.size();
+  c->X.t1 = p1->P.total_tiles;
+  c->X.ready = c->d_ready;
+  c->X.blk0 = c->d_blk0;
+  c->X.epoch = c->d_epoch;
+  *out = c;
+  return 0;
+}
+
+int tc_launch_chain(TcChain* c, cudaStream_t st) {
+  if (!c) return -1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(c->grid, 1, 1);
+  cfg.blockDim = dim3(192, 1, 1);
+  cfg.dynamicSmemBytes = c->smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 2;
+  return cudaLaunchKernelEx(&cfg, k_tc_chain<3>, c->p1->P, c->p2->P, c->X) == cudaSuccess ? 0 : -1;
+}
+
+// median device times of 9 chained launches and of 9 pairs of separate launches
+int tc_time_chain(TcChain* c, TcPlan* p1, TcPlan* p2, cudaStream_t st, double* ms_chain, double* ms_sep) {
+  constexpr int R = 9;
+  cudaEvent_t ev[R + 1];
+  for (auto& e : ev) cudaEventCreate(&e);
+  float a[R], b[R];
+  for (int pass = 0; pass < 2; ++pass) {
+    float* ms = pass ? b : a;
+    for (int w = 0; w < 2; ++w) {
+      if (pass) {
+        launch_variant(p1, st);
+        launch_variant(p2, st);
+      } else {
+        tc_launch_chain(c, st);
+      }
+    }
+    cudaEventRecord(ev[0], st);
+    for (int i = 0; i < R; ++i) {
+      if (pass) {
+        launch_variant(p1, st);
+        launch_variant(p2, st);
+      } else {
+        tc_launch_chain(c, st);
+      }
+      cudaEventRecord(ev[i + 1], st);
+    }
+    cudaEventSynchronize(ev[R]);
+    for (int i = 0; i < R; ++i) cudaEventElapsedTime(&ms[i], ev[i], ev[i + 1]);
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  std::sort(a, a + R);
+  std::sort(b, b + R);
+  *ms_chain = a[R / 2];
+  *ms_sep = b[R / 2];
+  int err = 0;
+  cudaMemcpy(&err, p1->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (cudaGetLastError() != cudaSuccess || err) return -1;
+  return 0;
+}
+
+void tc_reset_chain(TcChain* c, cudaStream_t st) {
+  if (!c) return;
+  int nblk = 0;
+  for (const TcProb& pr : c->p1->probs_h) nblk += pr.tiles_m;
+  cudaMemsetAsync(c->d_ready, 0, sizeof(unsigned long long) * nblk, st);
+  cudaMemsetAsync(c->d_epoch, 0, 2 * sizeof(unsigned long long), st);
+}
+
+void tc_destroy_chain(TcChain* c) {
+  if (!c) return;
+  if (c->d_ord) cudaFree(c->d_ord);
+  if (c->d_blk0) cudaFree(c->d_blk0);
+  if (c->d_ready) cudaFree(c->d_ready);
+  if (c->d_epoch) cudaFree(c->d_epoch);
+  delete c;
 }
 
 }  // namespace vgtb

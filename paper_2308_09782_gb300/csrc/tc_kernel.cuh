@@ -95,6 +95,11 @@ struct TcPlan {
   int* d_cofs = nullptr;    // planned column tiles of every system
   int grid = 0, smem = 0, variant = 0, epi = 0, wmax = 0;
   bool skip = false;
+  // host copies for the chained schedule: the problem table, every system's
+  // column-tile starts and the modelled time of every tile
+  std::vector<TcProb> probs_h;
+  std::vector<std::vector<int>> starts_h;
+  std::vector<double> cost_h;
 };
 
 // ----------------------------------------------------------------------------

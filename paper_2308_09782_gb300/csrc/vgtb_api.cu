@@ -116,6 +116,7 @@ struct vgtb_ctx {
   // tcgen05 plans
   TcPlan* tc1 = nullptr;
   TcPlan* tc2 = nullptr;
+  TcChain* tcc = nullptr;  // both products in one launch (null: two launches)
   // block-sparse first product (every atom 4 orbitals; product1 BLOCKS, or AUTO on the FP64 path)
   bool bsr = false;
   BsrItem* d_bsr = nullptr;
@@ -1042,7 +1043,11 @@ int enqueue_step(vgtb_ctx* ctx, cudaEvent_t* ev) {
   if (ctx->bsr)
     launch_bsr(ctx->d_bsr, ctx->d_bsrsys, ctx->n_items, ctx->bsr_units_max, ctx->bsr_units_total, ctx->d_bsr_u0,
                ctx->d_bsr_ctr, ctx->split ? 0 : 1, ctx->bsr_tg_max, ctx->d_step, st);
-  if (ctx->split) {
+  if (ctx->split && ctx->tcc) {
+    // both products in one launch: its time counts as product 1's
+    TRY(tc_launch_chain(ctx->tcc, st) == 0 ? VGTB_OK : fail(ctx, VGTB_E_CUDA, "chained tcgen05 launch failed"));
+    if (ev) CK(cudaEventRecordWithFlags(ev[4], st, evflag));
+  } else if (ctx->split) {
     if (!ctx->bsr)
       TRY(tc_launch(ctx->tc1, st) == 0 ? VGTB_OK : fail(ctx, VGTB_E_CUDA, "tcgen05 product 1 launch failed"));
     if (ev) CK(cudaEventRecordWithFlags(ev[4], st, evflag));
@@ -1123,7 +1128,11 @@ int check_status(vgtb_ctx* ctx) {
   }
   if (!ctx->split) return VGTB_OK;
   const int tc = tc_status(ctx->tc1, ctx->stream) | tc_status(ctx->tc2, ctx->stream);
-  if (tc) return fail(ctx, VGTB_E_TIMEOUT, "tcgen05 product reported status %d (bounded wait expired)", tc);
+  if (tc) {
+    // an aborted chained launch left its block counts short: start them again
+    if (ctx->tcc) tc_reset_chain(ctx->tcc, ctx->stream);
+    return fail(ctx, VGTB_E_TIMEOUT, "tcgen05 product reported status %d (bounded wait expired)", tc);
+  }
   return VGTB_OK;
 }
 
@@ -1179,6 +1188,8 @@ int vgtb_create_batch(vgtb_ctx** out, int n_sys, const vgtb_system* sys, int n_t
     return bail(fail(ctx, VGTB_E_INVALID, "unknown integrator %d", ctx->opt.integrator));
   if (ctx->opt.scc != VGTB_SCC_ON && ctx->opt.scc != VGTB_SCC_FROZEN)
     return bail(fail(ctx, VGTB_E_INVALID, "unknown scc mode %d", ctx->opt.scc));
+  if (ctx->opt.chain < VGTB_CHAIN_AUTO || ctx->opt.chain > VGTB_CHAIN_ON)
+    return bail(fail(ctx, VGTB_E_INVALID, "unknown chain mode %d", ctx->opt.chain));
   if (ctx->opt.product1 < VGTB_P1_AUTO || ctx->opt.product1 > VGTB_P1_BLOCKS)
     return bail(fail(ctx, VGTB_E_INVALID, "unknown product1 form %d", ctx->opt.product1));
   ctx->split = ctx->opt.precision == VGTB_SPLIT_BF16X3;
@@ -1485,6 +1496,25 @@ int vgtb_create_batch(vgtb_ctx** out, int n_sys, const vgtb_system* sys, int n_t
     if (tc_build_plans(views, ctx->items_h, ctx->opt.timeout_ns, ctx->opt.autotune, ctx->opt.tile_variant, ctx->stream,
                        ctx->bsr ? nullptr : &ctx->tc1, &ctx->tc2, &msg))
       return bail(fail(ctx, VGTB_E_CUDA, "tcgen05 plan: %s", msg.c_str()));
+    if (ctx->opt.chain != VGTB_CHAIN_OFF && tc_chainable(ctx->tc1, ctx->tc2)) {
+      if (tc_build_chain(ctx->tc1, ctx->tc2, &ctx->tcc, &msg))
+        return bail(fail(ctx, VGTB_E_CUDA, "tcgen05 chained plan: %s", msg.c_str()));
+      if (ctx->opt.chain == VGTB_CHAIN_AUTO) {
+        double ms_chain = 0, ms_sep = 0;
+        // a launch that failed or ran into the wait limit keeps two launches
+        const int tr = tc_time_chain(ctx->tcc, ctx->tc1, ctx->tc2, ctx->stream, &ms_chain, &ms_sep);
+        if (tr || ms_chain >= ms_sep) {
+          tc_destroy_chain(ctx->tcc);
+          ctx->tcc = nullptr;
+        }
+        if (tr) {
+          cudaStreamSynchronize(ctx->stream);
+          cudaGetLastError();
+          tc_clear_error(ctx->tc1);
+          tc_clear_error(ctx->tc2);
+        }
+      }
+    }
   }
   if (ctx->opt.init == VGTB_INIT_GROUND) {
     for (int s = 0; s < n_sys; ++s) {
@@ -1873,7 +1903,9 @@ int vgtb_tile_config(const vgtb_ctx* ctx, int product, int* cfg) {
     cfg[3] = 0;
     return VGTB_OK;
   }
-  return tc_plan_info(product == 1 ? ctx->tc1 : ctx->tc2, cfg) == 0 ? VGTB_OK : VGTB_E_STATE;
+  if (tc_plan_info(product == 1 ? ctx->tc1 : ctx->tc2, cfg)) return VGTB_E_STATE;
+  if (ctx->tcc) cfg[2] += 16;  // both products in one launch
+  return VGTB_OK;
 }
 
 const char* vgtb_last_error(const vgtb_ctx* ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
@@ -1883,6 +1915,7 @@ void vgtb_destroy(vgtb_ctx* ctx) {
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   drop_graph(ctx);
   for (auto e : ctx->ev) cudaEventDestroy(e);
+  tc_destroy_chain(ctx->tcc);
   tc_destroy_plan(ctx->tc1);
   tc_destroy_plan(ctx->tc2);
   for (void* p : ctx->allocs) cudaFree(p);

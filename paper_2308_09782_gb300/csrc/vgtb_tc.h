@@ -47,5 +47,18 @@ int tc_launch(TcPlan* p, cudaStream_t st);
 int tc_status(TcPlan* p, cudaStream_t st);  // 0 or the plan's device error word
 void tc_destroy_plan(TcPlan* p);
 int tc_plan_variant(const TcPlan* p);  // index of the tile variant the plan uses
+void tc_clear_error(TcPlan* p);        // zero the plan's device error word
+
+// Chained schedule: both products in one launch (tc_chain.cuh), over the
+// tables of two plans that it does not own (2-SM pair, classic schedule,
+// 64-column stages: tc_chainable).  tc_time_chain times it against the two
+// separate launches (median of 9 each; -1 if a launch failed or timed out).
+struct TcChain;
+bool tc_chainable(const TcPlan* p1, const TcPlan* p2);
+int tc_build_chain(const TcPlan* p1, const TcPlan* p2, TcChain** out, std::string* msg);
+int tc_launch_chain(TcChain* c, cudaStream_t st);
+int tc_time_chain(TcChain* c, TcPlan* p1, TcPlan* p2, cudaStream_t st, double* ms_chain, double* ms_sep);
+void tc_reset_chain(TcChain* c, cudaStream_t st);  // zero the block counts and the launch count
+void tc_destroy_chain(TcChain* c);
 
 }  // namespace vgtb

@@ -30,6 +30,9 @@ P1_DENSE = 1
 P1_BLOCKS = 2
 SCC_ON = 0
 SCC_FROZEN = 1
+CHAIN_AUTO = 0
+CHAIN_OFF = 1
+CHAIN_ON = 2
 KERNEL_CLASSES = ["obs", "scc", "phase", "gemm1", "gemm2", "leap"]
 
 EXPORTS = ["vgtb_default_options", "vgtb_create", "vgtb_create_batch", "vgtb_set_density",
@@ -58,7 +61,8 @@ class VgtbOptions(C.Structure):
                 ("obs_stride", C.c_int), ("graph_steps", C.c_int), ("autotune", C.c_int),
                 ("scc_tol", C.c_double), ("scc_max_iter", C.c_int),
                 ("integrator", C.c_int), ("cn_iter", C.c_int), ("cn_tol", C.c_double),
-                ("tile_variant", C.c_int * 2), ("product1", C.c_int), ("scc", C.c_int)]
+                ("tile_variant", C.c_int * 2), ("product1", C.c_int), ("scc", C.c_int),
+                ("chain", C.c_int)]
 
 
 _lib = None
@@ -341,6 +345,8 @@ class Context:
             base += ", planned column widths"
         if cfg[2] & 4:
             base += ", zero k-panels skipped"
+        if cfg[2] & 16:
+            base += ", both products in one launch"
         return {"tile_n": cfg[0], "stages": cfg[1], "schedule": base, "pair": bool(cfg[3])}
 
     def kernel_stats(self):

@@ -133,11 +133,11 @@ def _big_oracle(which):
     return O.propagate(systems[which], fields[which], BIG_ORACLE_STEPS[which], D, ctx=ctx)
 
 
-def _big_run(ids, precision, nsteps=BIG_STEPS, densities=False):
+def _big_run(ids, precision, nsteps=BIG_STEPS, densities=False, **opts):
     from paper_2308_09782_gb300 import vgtb
     systems, fields = _big_systems()
     c = vgtb.Context([systems[i] for i in ids], traj_sys=list(range(len(ids))), precision=precision,
-                     init=vgtb.INIT_USER, graph_steps=10)
+                     init=vgtb.INIT_USER, graph_steps=10, **opts)
     for s, gid in enumerate(ids):
         _, D = _big_start(gid)
         for k, Dk in enumerate(D):
@@ -183,6 +183,23 @@ def test_config5_sizes_fp64_batch_vs_oracle_and_single_runs():
           f"({BIG_ORACLE_STEPS[1]} steps)")
     assert err_d216 <= 1e-10
     assert err_d512 <= 1e-10
+
+
+def test_config5_sizes_chained_products_equal_two_launches():
+    """Split form, 216 atoms (Np = 896: row blocks of 256 with a half-empty last
+    one, column tiles across the Re/Im boundary of W) and 512 atoms on 8 k-points
+    in one context: both products in one launch (product 2 tiles waiting for the
+    rows of W they read) give the same propagation as two launches, bit for bit,
+    with the same tile variants (product 2 on planned column widths)."""
+    from paper_2308_09782_gb300 import vgtb
+    opts = dict(tile_variant=[0, 7])
+    one = _big_run([0, 1], vgtb.SPLIT_BF16X3, densities=True, chain=vgtb.CHAIN_ON, **opts)
+    two = _big_run([0, 1], vgtb.SPLIT_BF16X3, densities=True, chain=vgtb.CHAIN_OFF, **opts)
+    for gid in (0, 1):
+        assert np.array_equal(one[gid][0], two[gid][0])
+        assert np.array_equal(one[gid][1], two[gid][1])
+        for k in (0, 7):
+            assert np.array_equal(one[gid][3][k], two[gid][3][k])
 
 
 def test_config5_sizes_split_batch_vs_oracle_and_fp64():

@@ -140,6 +140,29 @@ def test_zero_panel_skipping_matches_the_dense_product(variant):
             assert np.array_equal(a.get_density(0, 0), b.get_density(0, 0))
 
 
+@pytest.mark.parametrize("tv", [[0, 0], [0, 7], [5, 7]])
+def test_chained_products_equal_two_launches(tv):
+    """Both products in one launch: product 2 tiles start as soon as the 256-row
+    blocks of W they read are stored (bounded waits on per-block counts, an epoch
+    per launch so nothing is reset).  Same tile variants, so the propagation
+    equals two launches bit for bit: 512 atoms, 50 steps (graphs of 50 launches,
+    so the epoch advances across replays).  Product 1 on single CTAs (variant 5)
+    cannot be chained: the option then keeps two launches."""
+    from paper_2308_09782_gb300 import vgtb
+    name, nsteps = "si512_kick", 50
+    with gpu_run(name, nsteps, precision=vgtb.SPLIT_BF16X3, tile_variant=tv, chain=vgtb.CHAIN_ON,
+                 graph_steps=50) as a, \
+            gpu_run(name, nsteps, precision=vgtb.SPLIT_BF16X3, tile_variant=tv, chain=vgtb.CHAIN_OFF) as b:
+        chained = "one launch" in a.tile_config(1)["schedule"]
+        assert chained == (tv[0] != 5)
+        assert "one launch" not in b.tile_config(1)["schedule"]
+        Ja, Ea, _ = a.observables(0)
+        Jb, Eb, _ = b.observables(0)
+        assert np.array_equal(Ja, Jb)
+        assert np.array_equal(Ea, Eb)
+        assert np.array_equal(a.get_density(0, 0), b.get_density(0, 0))
+
+
 def test_split_rerun_bitwise_and_autotuned_variants_agree():
     """The stream-K fixup sums partials in a fixed order: reruns are bitwise equal.
     The autotuner's choice (stream-K or classic tiles, 128 or 256 wide) stays within
