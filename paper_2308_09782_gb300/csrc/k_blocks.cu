@@ -428,9 +428,42 @@ __global__ void __launch_bounds__(kSccThreads) k_scc_atoms(const DevSys* __restr
   }
 }
 
+// The trajectory's totals at level n from the per-CTA partials of k_scc_eps, in a
+// fixed order (lane-strided sums, then a butterfly): J (Eq. 14), the energy, and
+// the checks of the level.  Run by one warp: the last CTA of k_scc_eps, or a
+// finisher CTA of k_phase_split (the split form's step, where the phase build
+// does not wait for these totals).
+__device__ void scc_finish(DevTraj& T, const DevSys& S, int n, int record, int lane) {
+  const int myblk = (S.nat + kSccRows - 1) / kSccRows;
+  double v[6] = {0, 0, 0, 0, 0, 0};  // Tx, Ty, Tz, E_band, dq.eps, electron count
+  for (int c = lane; c < myblk; c += 32) {
+    const double* cp = T.cpart + 6LL * c;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) v[i] += cp[i];
+  }
+#pragma unroll
+  for (int i = 0; i < 6; ++i) v[i] = warp_sum(v[i]);
+  if (lane == 0) {
+    const double J0 = -v[0] * S.inv_omega, J1 = -v[1] * S.inv_omega, J2 = -v[2] * S.inv_omega;
+    const double E = v[3] + 0.5 * v[4];
+    if (record) {
+      T.J[3LL * n] = J0;
+      T.J[3LL * n + 1] = J1;
+      T.J[3LL * n + 2] = J2;
+      T.E[n] = E;
+    }
+    int st = 0;
+    if (!isfinite(J0) || !isfinite(J1) || !isfinite(J2) || !isfinite(E) || !isfinite(v[5])) st |= ST_NONFINITE;
+    if (fabs(v[5] - S.nel) > 1e-6 * fmax(1.0, S.nel)) st |= ST_DRIFT;
+    if (st) atomicOr(T.status, st);
+  }
+}
+
+// finish = 1: the last CTA of each trajectory runs scc_finish; finish = 0: the
+// CTAs only store their partials (the step's k_phase_split finishes them).
 __global__ void __launch_bounds__(kSccThreads) k_scc_eps(const DevSys* __restrict__ sysv, DevTraj* trj, int n_traj,
                                                         int nblk, const int* __restrict__ step, int fixed_step,
-                                                        int record) {
+                                                        int record, int finish) {
   pdl_wait();
   pdl_trigger();
   constexpr int NW = kSccThreads / 32;
@@ -445,10 +478,11 @@ __global__ void __launch_bounds__(kSccThreads) k_scc_eps(const DevSys* __restric
   const int n = fixed_step >= 0 ? fixed_step : *step;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int I = b * kSccRows + warp;  // one warp per row of gamma
-  // A(t_n), read now so that the last CTA's serial tail does not wait for it
-  double An[3] = {0.0, 0.0, 0.0};
-  if (tid == 0 && T.af && T.A)
-    for (int a = 0; a < 3; ++a) An[a] = T.A[3 * n + a];
+  if (tid == 0 && b == 0 && T.af) {
+    // A(t_n)/c in FP32 for the phase build
+    constexpr double inv_c = 1.0 / kLight;
+    for (int a = 0; a < 3; ++a) T.af[a] = (float)((T.A ? T.A[3 * n + a] : 0.0) * inv_c);
+  }
   if (lane == 0)
 #pragma unroll
     for (int i = 0; i < 6; ++i) red[warp][i] = 0.0;
@@ -496,7 +530,7 @@ __global__ void __launch_bounds__(kSccThreads) k_scc_eps(const DevSys* __restric
     }
   }
   __syncthreads();
-  // the CTA's partial in a fixed order, then the last CTA adds the partials
+  // the CTA's partial in a fixed order, then (finish) the last CTA adds the partials
   if (tid == 0) {
     double* cp = T.cpart + 6LL * b;
 #pragma unroll
@@ -505,39 +539,27 @@ __global__ void __launch_bounds__(kSccThreads) k_scc_eps(const DevSys* __restric
       for (int w = 1; w < NW; ++w) v += red[w][i];
       cp[i] = v;
     }
-    __threadfence();
-    s_last = (atomicAdd(T.ticket, 1) == myblk - 1);
+    if (finish) {
+      __threadfence();
+      s_last = (atomicAdd(T.ticket, 1) == myblk - 1);
+    }
   }
+  if (!finish) return;
   __syncthreads();
   if (!s_last || warp != 0) return;
   __threadfence();
-  double v[6] = {0, 0, 0, 0, 0, 0};  // Tx, Ty, Tz, E_band, dq.eps, electron count
-  for (int c = lane; c < myblk; c += 32) {
-    const double* cp = T.cpart + 6LL * c;
-#pragma unroll
-    for (int i = 0; i < 6; ++i) v[i] += cp[i];
-  }
-#pragma unroll
-  for (int i = 0; i < 6; ++i) v[i] = warp_sum(v[i]);
-  if (lane == 0) {
-    const double J0 = -v[0] * S.inv_omega, J1 = -v[1] * S.inv_omega, J2 = -v[2] * S.inv_omega;
-    const double E = v[3] + 0.5 * v[4];
-    if (record) {
-      T.J[3LL * n] = J0;
-      T.J[3LL * n + 1] = J1;
-      T.J[3LL * n + 2] = J2;
-      T.E[n] = E;
-    }
-    if (T.af) {
-      constexpr double inv_c = 1.0 / kLight;
-      for (int a = 0; a < 3; ++a) T.af[a] = (float)(An[a] * inv_c);
-    }
-    int st = 0;
-    if (!isfinite(J0) || !isfinite(J1) || !isfinite(J2) || !isfinite(E) || !isfinite(v[5])) st |= ST_NONFINITE;
-    if (fabs(v[5] - S.nel) > 1e-6 * fmax(1.0, S.nel)) st |= ST_DRIFT;
-    if (st) atomicOr(T.status, st);
-    *T.ticket = 0;
-  }
+  scc_finish(T, S, n, record, lane);
+  if (lane == 0) *T.ticket = 0;
+}
+
+void launch_scc(const DevSys* sys, DevTraj* trj, int n_traj, const int* step, int stride, int fixed_step,
+                int record, int max_nat, int atoms_done, cudaStream_t st, int finish) {
+  const int nblk_a = (max_nat + kAtomsPerCta - 1) / kAtomsPerCta;
+  if (!atoms_done)
+    launch_pdl(k_scc_atoms, n_traj * nblk_a, kSccThreads, 0, st, sys, trj, n_traj, nblk_a, step, stride, fixed_step,
+               record);
+  const int nblk = (max_nat + kSccRows - 1) / kSccRows;
+  launch_pdl(k_scc_eps, n_traj * nblk, kSccThreads, 0, st, sys, trj, n_traj, nblk, step, fixed_step, record, finish);
 }
 
 int scc_configure(int max_nat) {
@@ -545,15 +567,6 @@ int scc_configure(int max_nat) {
   return 0;
 }
 
-void launch_scc(const DevSys* sys, DevTraj* trj, int n_traj, const int* step, int stride, int fixed_step,
-                int record, int max_nat, int atoms_done, cudaStream_t st) {
-  const int nblk_a = (max_nat + kAtomsPerCta - 1) / kAtomsPerCta;
-  if (!atoms_done)
-    launch_pdl(k_scc_atoms, n_traj * nblk_a, kSccThreads, 0, st, sys, trj, n_traj, nblk_a, step, stride, fixed_step,
-               record);
-  const int nblk = (max_nat + kSccRows - 1) / kSccRows;
-  launch_pdl(k_scc_eps, n_traj * nblk, kSccThreads, 0, st, sys, trj, n_traj, nblk, step, fixed_step, record);
-}
 
 // ---------------------------------------------------------------------------
 // Phase build, FP64 path: H_k(t)_{mu nu} = sum_images e^{-ik.L} v_{mu nu}(L) with
@@ -724,12 +737,21 @@ __device__ __forceinline__ void store_emb_f4(__nv_bfloat16* base, int Np, int r,
 // Four lanes per target.  Targets whose blocks have 4 columns and 16-byte aligned
 // values (tgt_vec: every sp3-sp3 pair) read each block row with float4 loads and
 // write 4 columns per store; other shapes take the element loop.
+// CTAs from `fin0` on (grid row 0 only, one per trajectory) are finishers: they add
+// up k_scc_eps's partials of the level (scc_finish), in parallel with the build.
 __global__ void __launch_bounds__(256, 4) k_phase_split(const DevSys* __restrict__ sysv,
-                                                     const DevTraj* __restrict__ trj,
+                                                     DevTraj* __restrict__ trj,
                                                      const DevItem* __restrict__ items,
-                                                     const int* __restrict__ wpre, int n_traj, int total) {
+                                                     const int* __restrict__ wpre, int n_traj, int total,
+                                                     int fin0, const int* __restrict__ step) {
   pdl_wait();
   pdl_trigger();
+  if (fin0 >= 0 && (int)blockIdx.x >= fin0) {
+    const int t = (int)blockIdx.x - fin0;
+    if (blockIdx.y != 0 || t >= n_traj || threadIdx.x >= 32) return;
+    scc_finish(trj[t], sysv[trj[t].sys], *step, 1, threadIdx.x);
+    return;
+  }
   const Unit U = unit_of_q(wpre, n_traj, total);
   if (!U.active) return;
   const int sub = threadIdx.x & 3;
@@ -820,12 +842,12 @@ __global__ void __launch_bounds__(256, 4) k_phase_split(const DevSys* __restrict
   }
 }
 
-void launch_phase_split(const DevSys* sys, const DevTraj* trj, const DevItem* items, const int* warp_prefix,
-                        int n_traj, int total_units, int max_nk, const int* step, cudaStream_t st) {
-  (void)step;  // the level's operands come from k_scc_eps
+void launch_phase_split(const DevSys* sys, DevTraj* trj, const DevItem* items, const int* warp_prefix,
+                        int n_traj, int total_units, int max_nk, const int* step, int finish, cudaStream_t st) {
   const int threads = 256;
   const int blocks = (total_units * 4 + threads - 1) / threads;
-  launch_pdl(k_phase_split, dim3(blocks, max_nk), threads, 0, st, sys, trj, items, warp_prefix, n_traj, total_units);
+  launch_pdl(k_phase_split, dim3(blocks + (finish ? n_traj : 0), max_nk), threads, 0, st, sys, trj, items,
+             warp_prefix, n_traj, total_units, finish ? blocks : -1, step);
 }
 
 // ---------------------------------------------------------------------------

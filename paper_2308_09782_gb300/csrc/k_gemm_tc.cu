@@ -511,22 +511,32 @@ int tc_variant_info(int v, int* out4) {
   return 0;
 }
 
+static bool variant_chainable(int v) {
+  const Variant& a = kVariants[v];
+  return a.pair && !a.streamk && a.kh == 1;
+}
+
 int tc_build_plans(const std::vector<TcSysView>& sys, const std::vector<DevItem>& items, long long timeout_ns,
                    int autotune, const int force_variant[2], cudaStream_t st, TcPlan** p1, TcPlan** p2,
-                   std::string* msg) {
+                   std::string* msg, TcPlan** alt1, TcPlan** alt2, double* ms_best) {
   if (force_variant[0] >= kNumVariants || force_variant[1] >= kNumVariants) {
     *msg = "tile variant index out of range";
     return -1;
   }
   if (p1) *p1 = nullptr;
   *p2 = nullptr;
+  if (alt1) *alt1 = nullptr;
+  if (alt2) *alt2 = nullptr;
+  if (ms_best) ms_best[0] = ms_best[1] = 0.0;
   if (configure_all() != cudaSuccess) {
     *msg = "cannot raise the shared-memory limit of the tcgen05 kernels";
     return -1;
   }
   for (int epi = p1 ? 0 : 1; epi < 2; ++epi) {
-    TcPlan* best = nullptr;
-    double best_ms = 1e30;
+    // every variant that ran, with its median time; the fastest is the plan, and
+    // the fastest chainable one (2-SM pair, classic, 64-column stages) is kept
+    // beside it when it is another variant, for the one-launch schedule
+    std::vector<std::pair<TcPlan*, double>> ran;
     // the pair kernel handles every Np (a multiple of 128), so variant 0 always applies
     const int fv = force_variant[epi];
     const int first = fv >= 0 ? fv : 0;
@@ -535,34 +545,41 @@ int tc_build_plans(const std::vector<TcSysView>& sys, const std::vector<DevItem>
       TcPlan* p = new TcPlan();
       if (build_one(sys, items, epi, v, timeout_ns, p, msg)) {
         tc_destroy_plan(p);
-        tc_destroy_plan(best);
+        for (auto& r : ran) tc_destroy_plan(r.first);
         return -1;
       }
+      double ms = 0.0;
       if (nv - first > 1) {
-        const double ms = time_plan(p, st);
+        ms = time_plan(p, st);
         int err = 0;
         cudaMemcpy(&err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost);
         if (cudaGetLastError() != cudaSuccess || err) {
           tc_destroy_plan(p);
           continue;
         }
-        if (ms < best_ms) {
-          tc_destroy_plan(best);
-          best = p;
-          best_ms = ms;
-        } else {
-          tc_destroy_plan(p);
-        }
-      } else {
-        best = p;
       }
+      ran.push_back({p, ms});
     }
-    if (!best) {
+    if (ran.empty()) {
       *msg = "no tcgen05 product variant ran";
       return -1;
     }
-    cudaMemset(best->d_err, 0, sizeof(int));
-    (epi == 0 ? *p1 : *p2) = best;
+    int best = 0, bestc = -1;
+    for (int i = 0; i < (int)ran.size(); ++i) {
+      if (ran[i].second < ran[best].second) best = i;
+      if (variant_chainable(ran[i].first->variant) && (bestc < 0 || ran[i].second < ran[bestc].second)) bestc = i;
+    }
+    TcPlan** alt = epi == 0 ? alt1 : alt2;
+    const bool keep_alt = alt && bestc >= 0 && bestc != best;
+    for (int i = 0; i < (int)ran.size(); ++i)
+      if (i != best && !(keep_alt && i == bestc)) tc_destroy_plan(ran[i].first);
+    cudaMemset(ran[best].first->d_err, 0, sizeof(int));
+    (epi == 0 ? *p1 : *p2) = ran[best].first;
+    if (ms_best) ms_best[epi] = ran[best].second;
+    if (keep_alt) {
+      cudaMemset(ran[bestc].first->d_err, 0, sizeof(int));
+      *alt = ran[bestc].first;
+    }
   }
   return 0;
 }
@@ -814,9 +831,10 @@ int tc_time_chain(TcChain* c, TcPlan* p1, TcPlan* p2, cudaStream_t st, double* m
   std::sort(b, b + R);
   *ms_chain = a[R / 2];
   *ms_sep = b[R / 2];
-  int err = 0;
+  int err = 0, errc = 0;
   cudaMemcpy(&err, p1->d_err, sizeof(int), cudaMemcpyDeviceToHost);
-  if (cudaGetLastError() != cudaSuccess || err) return -1;
+  cudaMemcpy(&errc, c->p1->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (cudaGetLastError() != cudaSuccess || err || errc) return -1;
   return 0;
 }
 

@@ -1007,7 +1007,8 @@ int enqueue_step_cn(vgtb_ctx* ctx, cudaEvent_t* ev, unsigned evflag) {
 
 // observables and SCC of the current level: split form k_obs_atoms_split + k_scc_eps,
 // FP64 paths k_obs + k_scc_atoms + k_scc_eps
-void launch_obs_scc(vgtb_ctx* ctx, cudaEvent_t* ev, unsigned evflag, int stride) {
+// finish = 0 (split step): the phase build's finisher CTAs add up J, E and the checks
+void launch_obs_scc(vgtb_ctx* ctx, cudaEvent_t* ev, unsigned evflag, int stride, int finish = 1) {
   cudaStream_t st = ctx->stream;
   const int nt = (int)ctx->trj.size();
   if (ctx->split)
@@ -1016,7 +1017,8 @@ void launch_obs_scc(vgtb_ctx* ctx, cudaEvent_t* ev, unsigned evflag, int stride)
     launch_obs(ctx->d_sys, ctx->d_trj, ctx->d_items, ctx->d_wpre, nt, ctx->total_warps, ctx->d_step,
                ctx->delta ? 1 : 0, -1, st);
   if (ev) cudaEventRecordWithFlags(ev[1], st, evflag);
-  launch_scc(ctx->d_sys, ctx->d_trj, nt, ctx->d_step, stride, -1, 1, ctx->max_nat, ctx->split ? 1 : 0, st);
+  launch_scc(ctx->d_sys, ctx->d_trj, nt, ctx->d_step, stride, -1, 1, ctx->max_nat, ctx->split ? 1 : 0, st,
+             ctx->split ? finish : 1);
 }
 
 int enqueue_step(vgtb_ctx* ctx, cudaEvent_t* ev) {
@@ -1031,11 +1033,11 @@ int enqueue_step(vgtb_ctx* ctx, cudaEvent_t* ev) {
   const int stride = ctx->opt.obs_stride > 0 ? ctx->opt.obs_stride : 1;
   if (ev) CK(cudaEventRecordWithFlags(ev[0], st, evflag));
   if (ctx->cn) return enqueue_step_cn(ctx, ev, evflag);
-  launch_obs_scc(ctx, ev, evflag, stride);
+  launch_obs_scc(ctx, ev, evflag, stride, ctx->split ? 0 : 1);
   if (ev) CK(cudaEventRecordWithFlags(ev[2], st, evflag));
   if (ctx->split)
     launch_phase_split(ctx->d_sys, ctx->d_trj, ctx->d_items, ctx->d_wpre, nt, ctx->total_warps, ctx->max_nk,
-                       ctx->d_step, st);
+                       ctx->d_step, 1, st);
   else
     launch_phase(ctx->d_sys, ctx->d_trj, ctx->d_items, ctx->d_wpre, nt, ctx->total_warps, ctx->d_step,
                  ctx->delta ? PH_FP64_DELTA : PH_FP64_PLAIN, -1, st);
@@ -1493,12 +1495,23 @@ int vgtb_create_batch(vgtb_ctx** out, int n_sys, const vgtb_system* sys, int n_t
       }
     }
     std::string msg;
+    // alt1 / alt2: the fastest chainable plans when the autotuner's picks are
+    // other variants (a stream-K schedule, say), so that the one-launch
+    // schedule competes against the fastest pair of separate launches
+    TcPlan *alt1 = nullptr, *alt2 = nullptr;
+    const bool want_alt = ctx->opt.chain != VGTB_CHAIN_OFF;
     if (tc_build_plans(views, ctx->items_h, ctx->opt.timeout_ns, ctx->opt.autotune, ctx->opt.tile_variant, ctx->stream,
-                       ctx->bsr ? nullptr : &ctx->tc1, &ctx->tc2, &msg))
+                       ctx->bsr ? nullptr : &ctx->tc1, &ctx->tc2, &msg, want_alt ? &alt1 : nullptr,
+                       want_alt ? &alt2 : nullptr))
       return bail(fail(ctx, VGTB_E_CUDA, "tcgen05 plan: %s", msg.c_str()));
-    if (ctx->opt.chain != VGTB_CHAIN_OFF && tc_chainable(ctx->tc1, ctx->tc2)) {
-      if (tc_build_chain(ctx->tc1, ctx->tc2, &ctx->tcc, &msg))
+    TcPlan* c1 = (alt1 && !tc_chainable(ctx->tc1, ctx->tc1)) ? alt1 : ctx->tc1;
+    TcPlan* c2 = (alt2 && !tc_chainable(ctx->tc2, ctx->tc2)) ? alt2 : ctx->tc2;
+    if (ctx->opt.chain != VGTB_CHAIN_OFF && tc_chainable(c1, c2)) {
+      if (tc_build_chain(c1, c2, &ctx->tcc, &msg)) {
+        if (alt1) tc_destroy_plan(alt1);
+        if (alt2) tc_destroy_plan(alt2);
         return bail(fail(ctx, VGTB_E_CUDA, "tcgen05 chained plan: %s", msg.c_str()));
+      }
       if (ctx->opt.chain == VGTB_CHAIN_AUTO) {
         double ms_chain = 0, ms_sep = 0;
         // a launch that failed or ran into the wait limit keeps two launches
@@ -1512,8 +1525,23 @@ int vgtb_create_batch(vgtb_ctx** out, int n_sys, const vgtb_system* sys, int n_t
           cudaGetLastError();
           tc_clear_error(ctx->tc1);
           tc_clear_error(ctx->tc2);
+          tc_clear_error(c1);
+          tc_clear_error(c2);
         }
       }
+    }
+    // the chain runs on its own plans: they become the context's products
+    if (ctx->tcc && c1 != ctx->tc1) {
+      tc_destroy_plan(ctx->tc1);
+      ctx->tc1 = c1;
+    } else if (alt1 && alt1 != ctx->tc1) {
+      tc_destroy_plan(alt1);
+    }
+    if (ctx->tcc && c2 != ctx->tc2) {
+      tc_destroy_plan(ctx->tc2);
+      ctx->tc2 = c2;
+    } else if (alt2 && alt2 != ctx->tc2) {
+      tc_destroy_plan(alt2);
     }
   }
   if (ctx->opt.init == VGTB_INIT_GROUND) {

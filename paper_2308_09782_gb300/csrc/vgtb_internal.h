@@ -263,14 +263,18 @@ enum PhaseMode : int {
 // delta: 0 = D itself (FP64), 1 = dD with the D0 part from obs0 (FP64)
 void launch_obs(const DevSys* sys, const DevTraj* trj, const DevItem* items, const int* warp_prefix,
                 int n_traj, int total_warps, const int* step, int delta, int fixed_step, cudaStream_t st);
-// atoms_done = 1: the per-atom sums were made by k_obs_atoms_split (split form)
+// atoms_done = 1: the per-atom sums were made by k_obs_atoms_split (split form);
+// finish = 0: J, E and the checks of the level are left to launch_phase_split's
+// finisher CTAs (the split form's step), else the last CTA of k_scc_eps does them
 void launch_scc(const DevSys* sys, DevTraj* trj, int n_traj, const int* step, int stride,
-                int fixed_step, int record, int max_nat, int atoms_done, cudaStream_t st);
+                int fixed_step, int record, int max_nat, int atoms_done, cudaStream_t st, int finish = 1);
 void launch_obs_atoms_split(const DevSys* sys, DevTraj* trj, const DevItem* items, int n_traj, int max_nat,
                             const int* step, int stride, int fixed_step, int record, cudaStream_t st);
-// grid rows = max_nk: row y builds k-points y, y + max_nk, ... of every target
-void launch_phase_split(const DevSys* sys, const DevTraj* trj, const DevItem* items, const int* warp_prefix,
-                        int n_traj, int total_units, int max_nk, const int* step, cudaStream_t st);
+// grid rows = max_nk: row y builds k-points y, y + max_nk, ... of every target;
+// finish = 1 adds one CTA per trajectory that finishes the level's J, E and
+// checks from k_scc_eps's partials (launched with finish = 0)
+void launch_phase_split(const DevSys* sys, DevTraj* trj, const DevItem* items, const int* warp_prefix,
+                        int n_traj, int total_units, int max_nk, const int* step, int finish, cudaStream_t st);
 void launch_to_planar_f32(const double2* src, float* dst, int Np, cudaStream_t st);
 void launch_phase(const DevSys* sys, const DevTraj* trj, const DevItem* items, const int* warp_prefix,
                   int n_traj, int total_warps, const int* step, int mode, int fixed_step, cudaStream_t st);

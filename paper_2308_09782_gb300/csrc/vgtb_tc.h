@@ -34,10 +34,14 @@ struct TcSysView {
 // force_variant[p] >= 0 uses that tile variant for product p+1; otherwise variant
 // 0, or with autotune the fastest candidate (median of 9 timed launches).
 // p1 == nullptr builds product 2 only (the first product runs block-sparse).
+// When autotuning, *alt1 / *alt2 (if given) receive the fastest chainable plan
+// of each product (tc_chainable) when that is not already the chosen plan, else
+// nullptr; the caller owns them.  ms_best[2] (if given) receives the median
+// times of the chosen plans (0 without autotuning).
 // Returns 0 on success, else fills *msg.
 int tc_build_plans(const std::vector<TcSysView>& sys, const std::vector<DevItem>& items, long long timeout_ns,
                    int autotune, const int force_variant[2], cudaStream_t st, TcPlan** p1, TcPlan** p2,
-                   std::string* msg);
+                   std::string* msg, TcPlan** alt1 = nullptr, TcPlan** alt2 = nullptr, double* ms_best = nullptr);
 int tc_num_variants();
 // {tile width, pipeline stages, schedule (0 classic, 1 stream-K, 2 classic waves + stream-K rest), 2-SM pair}
 int tc_variant_info(int v, int* out4);
@@ -51,8 +55,9 @@ void tc_clear_error(TcPlan* p);        // zero the plan's device error word
 
 // Chained schedule: both products in one launch (tc_chain.cuh), over the
 // tables of two plans that it does not own (2-SM pair, classic schedule,
-// 64-column stages: tc_chainable).  tc_time_chain times it against the two
-// separate launches (median of 9 each; -1 if a launch failed or timed out).
+// 64-column stages: tc_chainable).  tc_time_chain times it against two
+// separate launches of p1 and p2, which may be other plans than the chain's
+// (median of 9 each; -1 if a launch failed or timed out).
 struct TcChain;
 bool tc_chainable(const TcPlan* p1, const TcPlan* p2);
 int tc_build_chain(const TcPlan* p1, const TcPlan* p2, TcChain** out, std::string* msg);
