@@ -37,6 +37,7 @@ WORKLOAD = ("512-atom Si supercell (diamond 4x4x4, sigma=0.3 bohr), sp3, N=2048 
             "kick A_x=0.001 au, dt=0.2 au, SCC on")
 AU_FS = 0.0241888432658
 P1 = {"auto": 0, "dense": 1, "blocks": 2}     # vgtb_options.product1
+CHAIN = {"auto": 0, "off": 1, "on": 2}       # vgtb_options.chain
 
 
 def parse():
@@ -59,6 +60,8 @@ def parse():
                    help="timed steps of the batched form inside the headline run (0 = skip)")
     p.add_argument("--product1", choices=["auto", "dense", "blocks"], default="auto",
                    help="form of the split path's first product (vgtb_options.product1)")
+    p.add_argument("--chain", choices=["auto", "off", "on"], default="auto",
+                   help="both tcgen05 products in one launch (vgtb_options.chain): auto = kept when faster at create")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--cpu-1thread-steps", type=int, default=1,
@@ -425,7 +428,8 @@ def native(args):
     if args.tiles != "auto":
         tile_opts = {"autotune": 0, "tile_variant": [int(x) for x in args.tiles.split(",")]}
     ctx = vgtb.Context(sysd, precision=vgtb.SPLIT_BF16X3, init=vgtb.INIT_GROUND,
-                       cuda_stream=stream.cuda_stream, graph_steps=50, product1=P1[args.product1], **tile_opts)
+                       cuda_stream=stream.cuda_stream, graph_steps=50, product1=P1[args.product1],
+                       chain=CHAIN[args.chain], **tile_opts)
     ctx.set_field(0, A[:n_need])
     tiles = {f"product{p}": ctx.tile_config(p) for p in (1, 2)}
     tiles["choice"] = ("autotuned at create: fastest of the tcgen05 tile variants (median of 9 launches)"
@@ -734,6 +738,7 @@ def run_batched(args, K, W, timing_start=False):
     ctx = vgtb.Context(systems, traj_sys=traj_sys, precision=vgtb.SPLIT_BF16X3,
                        init=vgtb.INIT_USER if timing_start else vgtb.INIT_GROUND,
                        cuda_stream=stream.cuda_stream, graph_steps=20, obs_stride=10, product1=P1[args.product1],
+                       chain=CHAIN[args.chain],
                        **tile_opts)
     if timing_start:
         for si, sd in enumerate(systems):

@@ -132,9 +132,12 @@ typedef struct {
   int chain;                /* split form, both products on the tcgen05 kernel: VGTB_CHAIN_AUTO (0,
                                default) runs them as one launch, with a product-2 tile starting
                                as soon as the rows of W it reads are stored (Eq. 6: X = S^-1 W^dagger
-                               needs W only), when that is faster at create than two launches;
-                               VGTB_CHAIN_OFF: two launches; VGTB_CHAIN_ON: one launch whenever
-                               the tile variants allow it (2-SM pairs, classic schedules) */
+                               needs W only), when that is faster at create than the two fastest
+                               separate launches (with autotune, the one launch runs on the
+                               fastest chainable variants, which may differ from the separate
+                               picks); VGTB_CHAIN_OFF: two launches; VGTB_CHAIN_ON: one launch
+                               whenever the tile variants allow it (2-SM pairs, classic
+                               schedules, 64-column stages) */
 } vgtb_options;
 
 #define VGTB_P1_AUTO     0
