@@ -1502,8 +1502,12 @@ int vgtb_create_batch(vgtb_ctx** out, int n_sys, const vgtb_system* sys, int n_t
     const bool want_alt = ctx->opt.chain != VGTB_CHAIN_OFF;
     if (tc_build_plans(views, ctx->items_h, ctx->opt.timeout_ns, ctx->opt.autotune, ctx->opt.tile_variant, ctx->stream,
                        ctx->bsr ? nullptr : &ctx->tc1, &ctx->tc2, &msg, want_alt ? &alt1 : nullptr,
-                       want_alt ? &alt2 : nullptr))
+                       want_alt ? &alt2 : nullptr)) {
+      // a failure in product 2 can follow a product 1 that already kept an alternate
+      if (alt1) tc_destroy_plan(alt1);
+      if (alt2) tc_destroy_plan(alt2);
       return bail(fail(ctx, VGTB_E_CUDA, "tcgen05 plan: %s", msg.c_str()));
+    }
     TcPlan* c1 = (alt1 && !tc_chainable(ctx->tc1, ctx->tc1)) ? alt1 : ctx->tc1;
     TcPlan* c2 = (alt2 && !tc_chainable(ctx->tc2, ctx->tc2)) ? alt2 : ctx->tc2;
     if (ctx->opt.chain != VGTB_CHAIN_OFF && tc_chainable(c1, c2)) {
