@@ -389,9 +389,11 @@ void launch_obs(const DevSys* sys, const DevTraj* trj, const DevItem* items, con
 //   k_scc_atoms: one warp per atom sums the partials of the atom's targets
 //                (targets are sorted by row atom): q_I, dq_I, and the atom's
 //                share of T_a and of the band energy;
-//   k_scc_eps:   kSccRows rows of eps = gamma dq per CTA, one per warp (Eq. 10); the last CTA
-//                of a trajectory adds up J (Eq. 14), the band energy and
-//                dq.eps/2 in a fixed order and runs the checks.
+//   k_scc_eps:   kSccRows rows of eps = gamma dq per CTA, one per warp (Eq. 10), and one
+//                partial of J, the band energy, dq.eps/2 and the electron count per CTA;
+//                scc_finish adds the partials in a fixed order (J of Eq. 14, the energy,
+//                the checks): run by the last CTA of k_scc_eps, or, in the split form's
+//                step, by a finisher CTA of k_phase_split.
 // ---------------------------------------------------------------------------
 constexpr int kSccThreads = 32 * kSccRowsPerCta;
 constexpr int kSccRows = kSccRowsPerCta;
